@@ -1,0 +1,175 @@
+"""CPU oracle for geodesic 3x3 chains -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package. The product path (``paper_1911_13074_gb300``)
+never imports it and has no CPU fallback.
+
+The arithmetic lives in ``oracle.c`` (plain C loops written from the paper's
+definitions, Section 2, Eq. 1-5; see the header of that file). This module
+builds it with gcc into ``oracle/_build/liboracle.so`` and converts numpy
+arrays to and from float64 around each call. uint8 and float32 values
+convert to float64 exactly and the forward operators only select, so the
+results convert back exactly.
+
+Parity pins: every function is checked against independent results in
+``tests/test_oracle_pins.py`` (brute-force windows, scipy's max/min filters,
+threshold decomposition with breadth-first search, a widest-path search for
+reconstruction, finite differences and a source-identity closed form for the
+backward pass).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+DILATE, ERODE = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc (plain -O2, no vector intrinsics)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            L = ctypes.c_long
+            I = ctypes.c_int
+            lib.oracle_step.argtypes = [P, P, P, L, L, I, I]
+            lib.oracle_step.restype = None
+            lib.oracle_chain.argtypes = [P, P, P, L, L, I, I, L]
+            lib.oracle_chain.restype = I
+            lib.oracle_reconstruct.argtypes = [P, P, P, L, L, I, I, L]
+            lib.oracle_reconstruct.restype = L
+            lib.oracle_window.argtypes = [P, P, L, L, L, I]
+            lib.oracle_window.restype = I
+            lib.oracle_chain_backward.argtypes = [P, P, P, P, P, L, L, I, I, L]
+            lib.oracle_chain_backward.restype = I
+            _lib = lib
+    return _lib
+
+
+def use_library(path):
+    """Load the oracle from another build of oracle.c (used by the mutation
+    tests, which compile deliberately broken copies). Returns the previous
+    library handle so the caller can restore it with ``restore_library``."""
+    global _lib
+    prev = _load()
+    lib = ctypes.CDLL(path)
+    for name in ("oracle_step", "oracle_chain", "oracle_reconstruct", "oracle_window",
+                 "oracle_chain_backward"):
+        fn, ref = getattr(lib, name), getattr(prev, name)
+        fn.argtypes, fn.restype = ref.argtypes, ref.restype
+    with _lock:
+        _lib = lib
+    return prev
+
+
+def restore_library(prev):
+    global _lib
+    with _lock:
+        _lib = prev
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _back(out64, like):
+    if like.dtype == np.float64:
+        return out64
+    return out64.astype(like.dtype)
+
+
+def _opcode(op):
+    return {"dilate": DILATE, "erode": ERODE, DILATE: DILATE, ERODE: ERODE}[op]
+
+
+def step(f, m, conn=8, op="dilate"):
+    """One elementary geodesic step (Eq. 3 / its dual); m=None: plain 3x3 step."""
+    lib = _load()
+    f64 = _f64(f)
+    m64 = None if m is None else _f64(m)
+    out = np.empty_like(f64)
+    H, W = f64.shape
+    lib.oracle_step(_ptr(f64), _ptr(m64), _ptr(out), H, W, conn, _opcode(op))
+    return _back(out, np.asarray(f))
+
+
+def chain(f, m, steps, conn=8, op="dilate"):
+    """Geodesic chain of `steps` elementary steps (Eq. 4); m=None: unmasked."""
+    lib = _load()
+    f64 = _f64(f)
+    m64 = None if m is None else _f64(m)
+    out = np.empty_like(f64)
+    H, W = f64.shape
+    rc = lib.oracle_chain(_ptr(f64), _ptr(m64), _ptr(out), H, W, conn, _opcode(op), int(steps))
+    if rc != 0:
+        raise MemoryError("oracle_chain failed")
+    return _back(out, np.asarray(f))
+
+
+def reconstruct(f, m, conn=8, op="dilate", max_steps=None):
+    """Reconstruction by dilation / erosion (Eq. 5). Returns (out, changing_steps)."""
+    lib = _load()
+    f64 = _f64(f)
+    m64 = _f64(m)
+    out = np.empty_like(f64)
+    H, W = f64.shape
+    if max_steps is None:
+        max_steps = H * W + 1
+    n = lib.oracle_reconstruct(_ptr(f64), _ptr(m64), _ptr(out), H, W, conn, _opcode(op), int(max_steps))
+    if n == -2:
+        raise MemoryError("oracle_reconstruct failed")
+    return _back(out, np.asarray(f)), int(n)
+
+
+def window(f, half_size, op="dilate"):
+    """Erosion / dilation by the clipped (2s+1)^2 square (Eq. 1-2)."""
+    lib = _load()
+    f64 = _f64(f)
+    out = np.empty_like(f64)
+    H, W = f64.shape
+    rc = lib.oracle_window(_ptr(f64), _ptr(out), H, W, int(half_size), _opcode(op))
+    if rc != 0:
+        raise MemoryError("oracle_window failed")
+    return _back(out, np.asarray(f))
+
+
+def chain_backward(f, m, grad_out, steps, conn=8, op="dilate"):
+    """Reverse mode of the masked chain. Returns (grad_marker, grad_mask) in float64."""
+    lib = _load()
+    f64, m64, g64 = _f64(f), _f64(m), _f64(grad_out)
+    gmk = np.empty_like(f64)
+    gms = np.empty_like(f64)
+    H, W = f64.shape
+    rc = lib.oracle_chain_backward(_ptr(f64), _ptr(m64), _ptr(g64), _ptr(gmk), _ptr(gms),
+                                   H, W, conn, _opcode(op), int(steps))
+    if rc != 0:
+        raise MemoryError("oracle_chain_backward failed")
+    return gmk, gms

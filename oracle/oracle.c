@@ -1,0 +1,227 @@
+/*
+ * CPU oracle for geodesic 3x3 chains. TEST INFRASTRUCTURE ONLY.
+ *
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg call
+ * this code. It shares nothing with the CUDA library (no header, no helper, no
+ * constant) and is written as the plain definitions from Zlaus & Mongus,
+ * "Efficient method for parallel computation of geodesic transformation on
+ * CPU" (IEEE TPDS 2019):
+ *
+ *   Section 2, Eq. 1-2  erosion / dilation by the square w_s(p), which is
+ *                       clipped to the image domain P (w_s(p) is a subset of P)
+ *   Section 2, Eq. 3    elementary geodesic erosion  max(eps_1(f), m)
+ *                       and its dual dilation        min(delta_1(f), m)
+ *   Section 2, Eq. 4    geodesic erosion/dilation of size s = s nested steps
+ *   Section 2, Eq. 5    reconstruction = the limit of the chain (iterate until
+ *                       a step changes nothing, as in Section 3.7, Algorithm 5)
+ *
+ * Every value is held as a double. uint8 and float32 images convert to double
+ * exactly, and the forward operators only select among their inputs, so the
+ * results convert back exactly. The backward pass (not in the paper) sums
+ * upstream gradients in double.
+ *
+ * Images are row-major, contiguous, H rows of W pixels; index y * W + x.
+ * conn = 8 uses the 3x3 square w_1; conn = 4 uses the cross (centre plus
+ * the four edge neighbours), which the paper does not use; it is this
+ * library's extension. Pixels outside the image are skipped, never padded.
+ */
+#include <stdlib.h>
+#include <string.h>
+
+enum { ORA_DILATE = 0, ORA_ERODE = 1 };
+
+/* neighbour k = (dy + 1) * 3 + (dx + 1); the cross keeps k in {1, 3, 4, 5, 7} */
+static int ora_in_shape(int conn, int dy, int dx)
+{
+    return conn == 8 || dy == 0 || dx == 0;
+}
+
+/* extreme of f over the clipped neighbourhood of (y, x): Eq. 1 (op = erode) or
+ * Eq. 2 (op = dilate) with s = 1; *k_out gets the lowest neighbour index k
+ * that attains it. */
+static double ora_extreme(const double *f, long H, long W, int conn, int op,
+                          long y, long x, int *k_out)
+{
+    double best = 0.0;
+    int have = 0, bestk = -1;
+    for (int dy = -1; dy <= 1; ++dy) {
+        for (int dx = -1; dx <= 1; ++dx) {
+            if (!ora_in_shape(conn, dy, dx)) continue;
+            long qy = y + dy, qx = x + dx;
+            if (qy < 0 || qy >= H || qx < 0 || qx >= W) continue;
+            double v = f[qy * W + qx];
+            int better = !have || (op == ORA_DILATE ? (v > best) : (v < best));
+            if (better) {
+                best = v;
+                bestk = (dy + 1) * 3 + (dx + 1);
+                have = 1;
+            }
+        }
+    }
+    if (k_out) *k_out = bestk;
+    return best;
+}
+
+/* One elementary geodesic step (Eq. 3 and its dual). m == NULL: no mask
+ * (a plain eps_1 / delta_1 step). */
+void oracle_step(const double *f, const double *m, double *out, long H, long W,
+                 int conn, int op)
+{
+    for (long y = 0; y < H; ++y) {
+        for (long x = 0; x < W; ++x) {
+            double v = ora_extreme(f, H, W, conn, op, y, x, NULL);
+            if (m) {
+                double mv = m[y * W + x];
+                if (op == ORA_DILATE) v = (mv < v) ? mv : v;  /* min(delta_1(f), m) */
+                else                  v = (mv > v) ? mv : v;  /* max(eps_1(f), m)   */
+            }
+            out[y * W + x] = v;
+        }
+    }
+}
+
+/* Geodesic erosion / dilation of size `steps` (Eq. 4): steps nested
+ * elementary steps, each computed from the whole previous image. */
+int oracle_chain(const double *f, const double *m, double *out, long H, long W,
+                 int conn, int op, long steps)
+{
+    long n = H * W;
+    if (n == 0) return 0;
+    memcpy(out, f, (size_t)n * sizeof(double));
+    if (steps <= 0) return 0;
+    double *tmp = (double *)malloc((size_t)n * sizeof(double));
+    if (!tmp) return -1;
+    for (long s = 0; s < steps; ++s) {
+        oracle_step(out, m, tmp, H, W, conn, op);
+        memcpy(out, tmp, (size_t)n * sizeof(double));
+    }
+    free(tmp);
+    return 0;
+}
+
+/* Reconstruction (Eq. 5): repeat elementary steps until one changes no pixel.
+ * Returns the number of steps that changed something, or -1 if max_steps
+ * steps all changed something (not converged), or -2 on allocation failure. */
+long oracle_reconstruct(const double *f, const double *m, double *out, long H,
+                        long W, int conn, int op, long max_steps)
+{
+    long n = H * W;
+    if (n == 0) return 0;
+    memcpy(out, f, (size_t)n * sizeof(double));
+    double *tmp = (double *)malloc((size_t)n * sizeof(double));
+    if (!tmp) return -2;
+    long changing = 0;
+    for (;;) {
+        if (changing >= max_steps) { changing = -1; break; }
+        oracle_step(out, m, tmp, H, W, conn, op);
+        int changed = 0;
+        for (long i = 0; i < n; ++i) {
+            if (tmp[i] != out[i]) { changed = 1; break; }
+        }
+        if (!changed) break;
+        memcpy(out, tmp, (size_t)n * sizeof(double));
+        ++changing;
+    }
+    free(tmp);
+    return changing;
+}
+
+/* Erosion / dilation by the clipped square w_s (Eq. 1-2). The window is the
+ * product {x-s..x+s} x {y-s..y+s} intersected with P, so its extreme is the
+ * extreme over rows of the extreme over columns; both loops run over the
+ * window itself (no running-extreme trick). */
+int oracle_window(const double *f, double *out, long H, long W, long s, int op)
+{
+    long n = H * W;
+    if (n == 0) return 0;
+    double *row = (double *)malloc((size_t)n * sizeof(double));
+    if (!row) return -1;
+    for (long y = 0; y < H; ++y) {
+        for (long x = 0; x < W; ++x) {
+            long x0 = x - s < 0 ? 0 : x - s, x1 = x + s >= W ? W - 1 : x + s;
+            double v = f[y * W + x0];
+            for (long q = x0 + 1; q <= x1; ++q) {
+                double u = f[y * W + q];
+                v = (op == ORA_DILATE) ? (u > v ? u : v) : (u < v ? u : v);
+            }
+            row[y * W + x] = v;
+        }
+    }
+    for (long y = 0; y < H; ++y) {
+        long y0 = y - s < 0 ? 0 : y - s, y1 = y + s >= H ? H - 1 : y + s;
+        for (long x = 0; x < W; ++x) {
+            double v = row[y0 * W + x];
+            for (long q = y0 + 1; q <= y1; ++q) {
+                double u = row[q * W + x];
+                v = (op == ORA_DILATE) ? (u > v ? u : v) : (u < v ? u : v);
+            }
+            out[y * W + x] = v;
+        }
+    }
+    free(row);
+    return 0;
+}
+
+/* Reverse mode of the masked chain (Eq. 4), which the paper does not cover.
+ *
+ * Step t maps f_{t-1} to f_t with f_t(p) = clamp(ext_{q in N(p)} f_{t-1}(q), m(p)).
+ * Routing rule at pixel p:
+ *   - the mask is selected when it is strictly beyond the neighbourhood
+ *     extreme (m(p) < v(p) for dilation, m(p) > v(p) for erosion); the upstream
+ *     gradient g_t(p) is then added to grad_mask(p);
+ *   - otherwise the gradient goes to the neighbour q = p + d_k, where k is the
+ *     lowest neighbour index attaining the extreme.
+ * Chain rule as a gather: g_{t-1}(q) = sum over k = 0..8 (in increasing k) of
+ * g_t(q - d_k) where pixel q - d_k is in the image and routed to its
+ * neighbour k. grad_mask accumulates over t = steps, steps-1, ..., 1.
+ * Forward states are all kept in memory. Returns 0, or -1 on allocation
+ * failure. */
+int oracle_chain_backward(const double *f0, const double *m, const double *gout,
+                          double *gmarker, double *gmask, long H, long W,
+                          int conn, int op, long steps)
+{
+    long n = H * W;
+    if (n == 0) return 0;
+    for (long i = 0; i < n; ++i) gmask[i] = 0.0;
+    memcpy(gmarker, gout, (size_t)n * sizeof(double));
+    if (steps <= 0) return 0;
+    double *states = (double *)malloc((size_t)n * (size_t)steps * sizeof(double));
+    double *gnew = (double *)malloc((size_t)n * sizeof(double));
+    int *sel = (int *)malloc((size_t)n * sizeof(int));
+    if (!states || !gnew || !sel) {
+        free(states); free(gnew); free(sel);
+        return -1;
+    }
+    memcpy(states, f0, (size_t)n * sizeof(double));
+    for (long t = 1; t < steps; ++t)
+        oracle_step(states + (t - 1) * n, m, states + t * n, H, W, conn, op);
+    for (long t = steps; t >= 1; --t) {
+        const double *fp = states + (t - 1) * n;
+        /* routing of step t: sel = neighbour index, or -1 for the mask */
+        for (long y = 0; y < H; ++y) {
+            for (long x = 0; x < W; ++x) {
+                int k;
+                double v = ora_extreme(fp, H, W, conn, op, y, x, &k);
+                double mv = m[y * W + x];
+                int to_mask = (op == ORA_DILATE) ? (mv < v) : (mv > v);
+                sel[y * W + x] = to_mask ? -1 : k;
+                if (to_mask) gmask[y * W + x] += gmarker[y * W + x];
+            }
+        }
+        for (long y = 0; y < H; ++y) {
+            for (long x = 0; x < W; ++x) {
+                double acc = 0.0;
+                for (int k = 0; k < 9; ++k) {
+                    int dy = k / 3 - 1, dx = k % 3 - 1;
+                    long py = y - dy, px = x - dx;
+                    if (py < 0 || py >= H || px < 0 || px >= W) continue;
+                    if (sel[py * W + px] == k) acc += gmarker[py * W + px];
+                }
+                gnew[y * W + x] = acc;
+            }
+        }
+        memcpy(gmarker, gnew, (size_t)n * sizeof(double));
+    }
+    free(states); free(gnew); free(sel);
+    return 0;
+}

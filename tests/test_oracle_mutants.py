@@ -1,0 +1,84 @@
+"""Mutation check of the oracle pins: plant plausible mistakes in copies of
+oracle.c (on the CPU) and require that the pins catch every one of them."""
+import os
+import shutil
+import subprocess
+import tempfile
+
+import pytest
+
+import oracle
+from tests import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
+
+# (name, original text, mutated text, pins expected to notice)
+MUTANTS = [
+    ("drop_right_column", "for (int dx = -1; dx <= 1; ++dx) {\n            if (!ora_in_shape",
+     "for (int dx = -1; dx <= 0; ++dx) {\n            if (!ora_in_shape"),
+    ("clamp_direction", "if (op == ORA_DILATE) v = (mv < v) ? mv : v;",
+     "if (op == ORA_DILATE) v = (mv > v) ? mv : v;"),
+    ("erode_clamp_direction", "else                  v = (mv > v) ? mv : v;",
+     "else                  v = (mv < v) ? mv : v;"),
+    ("clip_last_row", "if (qy < 0 || qy >= H || qx < 0 || qx >= W) continue;\n            double v",
+     "if (qy < 0 || qy >= H - 1 || qx < 0 || qx >= W) continue;\n            double v"),
+    ("cross_missing_vertical", "return conn == 8 || dy == 0 || dx == 0;", "return conn == 8 || dy == 0;"),
+    ("extra_step", "for (long s = 0; s < steps; ++s) {", "for (long s = 0; s <= steps; ++s) {"),
+    ("window_short_right", "x1 = x + s >= W ? W - 1 : x + s;", "x1 = x + s >= W ? W - 1 : x + s - (s > 0);"),
+    ("window_rows_short", "y1 = y + s >= H ? H - 1 : y + s;", "y1 = y + s >= H ? H - 1 : y + s - (s > 1);"),
+    ("reconstruct_partial_check", "for (long i = 0; i < n; ++i) {\n            if (tmp[i] != out[i])",
+     "for (long i = 0; i < n / 2; ++i) {\n            if (tmp[i] != out[i])"),
+    ("tie_highest_index", "(op == ORA_DILATE ? (v > best) : (v < best))",
+     "(op == ORA_DILATE ? (v >= best) : (v < best))"),
+    ("erode_tie_highest_index", "(op == ORA_DILATE ? (v > best) : (v < best))",
+     "(op == ORA_DILATE ? (v > best) : (v <= best))"),
+    ("mask_wins_ties", "int to_mask = (op == ORA_DILATE) ? (mv < v) : (mv > v);",
+     "int to_mask = (op == ORA_DILATE) ? (mv <= v) : (mv > v);"),
+    ("gather_transposed", "long py = y - dy, px = x - dx;", "long py = y + dy, px = x + dx;"),
+    ("gmask_overwrites", "if (to_mask) gmask[y * W + x] += gmarker[y * W + x];",
+     "if (to_mask) gmask[y * W + x] = gmarker[y * W + x];"),
+]
+
+PIN_TESTS = [
+    lambda: pins.test_window_matches_bruteforce_and_chain_on_tiny_images("dilate"),
+    lambda: pins.test_window_matches_bruteforce_and_chain_on_tiny_images("erode"),
+    lambda: pins.test_four_connected_chain_is_clipped_diamond("dilate"),
+    lambda: pins.test_masked_chain_threshold_decomposition(4, "dilate", "u8few"),
+    lambda: pins.test_masked_chain_threshold_decomposition(8, "erode", "u8few"),
+    lambda: pins.test_reconstruct_is_widest_path(8, "dilate", "u8"),
+    lambda: pins.test_reconstruct_is_widest_path(4, "erode", "f64"),
+    lambda: pins.test_backward_matches_finite_differences(8, "dilate"),
+    lambda: pins.test_backward_source_identity(4, "erode"),
+    lambda: pins.test_backward_tie_rule_lowest_index_and_marker_on_mask_tie(),
+    lambda: pins.test_backward_erosion_tie_rule(),
+]
+
+
+@pytest.fixture(scope="module")
+def workdir():
+    d = tempfile.mkdtemp(prefix="oracle_mutants_")
+    yield d
+    shutil.rmtree(d, ignore_errors=True)
+
+
+@pytest.mark.parametrize("name,orig,mut", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_mutant(name, orig, mut, workdir):
+    src = open(SRC).read()
+    assert orig in src, f"mutation site of {name} not found"
+    c_path = os.path.join(workdir, f"{name}.c")
+    so_path = os.path.join(workdir, f"{name}.so")
+    with open(c_path, "w") as fh:
+        fh.write(src.replace(orig, mut, 1))
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", so_path, c_path])
+    prev = oracle.use_library(so_path)
+    caught = []
+    try:
+        for t in PIN_TESTS:
+            try:
+                t()
+            except AssertionError:
+                caught.append(t)
+                break
+    finally:
+        oracle.restore_library(prev)
+    assert caught, f"no pin detected mutant {name}"
