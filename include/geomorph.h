@@ -1,0 +1,132 @@
+/*
+ * geomorph -- geodesic 3x3 chains on one NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of the library libgeomorph.so. Every function is extern "C", takes
+ * plain pointers and sizes, and returns a geo_status (0 = success). Nothing
+ * is thrown across the boundary.
+ *
+ * The operations follow Zlaus & Mongus, "Efficient method for parallel
+ * computation of geodesic transformation on CPU" (IEEE TPDS 2019):
+ *
+ *   image model        Section 2: f : P -> R, P = {0..X-1} x {0..Y-1},
+ *                      X = width, Y = height, stored row-major.
+ *   neighbourhood      Section 2, Eq. 1-2: the 3x3 square w_1(p) clipped to
+ *                      the image (pixels outside P are ignored, never padded).
+ *                      conn = 8 selects it; conn = 4 selects the cross
+ *                      {centre, left, right, up, down}, also clipped, which
+ *                      the paper does not use (an extension of this library).
+ *   elementary step    Section 2, Eq. 3: erosion  f' = max(eps_1(f), m),
+ *                      dilation f' = min(delta_1(f), m). Every step is
+ *                      computed from the whole previous image.
+ *   chain              Section 2, Eq. 4: `steps` nested elementary steps.
+ *   reconstruction     Section 2, Eq. 5: the limit of the chain, reached
+ *                      when a step changes no pixel (Section 3.7, Algorithm 5).
+ *   square window      Section 2, Eq. 1-2 with half size s: the clipped
+ *                      (2s+1)^2 window, computed as s unmasked 3x3 steps
+ *                      (the decomposition of Section 3.1).
+ *
+ * Common conventions
+ *   - Pointers named marker, mask, in, out, grad_* are DEVICE pointers owned
+ *     by the caller. The library reads marker/mask/in and writes out; it
+ *     never frees or keeps them after the call's GPU work completes.
+ *   - Element type: GEO_U8 (uint8_t), GEO_F32 (float), GEO_F64 (double).
+ *     NaN and negative zero are outside the contract.
+ *   - `pitch` is the row stride in ELEMENTS (pitch >= width), shared by all
+ *     image arguments of a call. Pixel (y, x) is at ptr[y * pitch + x].
+ *   - `out` may alias `marker` (in-place); `out` must not overlap `mask`.
+ *   - height == 0 or width == 0 is a no-op returning GEO_OK.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t, may be NULL for
+ *     the legacy default stream). Internal scratch memory is allocated
+ *     stream-ordered (cudaMallocAsync from a library-owned pool) and released
+ *     stream-ordered before the call returns.
+ *   - Errors a call can detect on the host (bad arguments, launch failure)
+ *     are returned directly. Errors detected on the device (a bounded wait
+ *     that expired, a reconstruction that did not converge) are recorded in
+ *     a per-device status word: read it with geo_device_status().
+ *   - One library instance serves every device; calls use the current device.
+ */
+#ifndef GEOMORPH_H
+#define GEOMORPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GEO_API __attribute__((visibility("default")))
+#else
+#define GEO_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { GEO_U8 = 0, GEO_F32 = 1, GEO_F64 = 2 } geo_dtype;
+
+typedef enum {
+    GEO_OK = 0,
+    GEO_ERR_ARG = -1,            /* invalid argument (pointer, size, pitch, conn, steps, aliasing) */
+    GEO_ERR_DTYPE = -2,          /* unsupported element type for this operation */
+    GEO_ERR_ALIGN = -3,          /* pointer not aligned to its element size */
+    GEO_ERR_CUDA = -4,           /* a CUDA runtime call failed (launch, allocation, ...) */
+    GEO_ERR_TIMEOUT = -5,        /* device: a bounded inter-block wait expired */
+    GEO_ERR_NOT_CONVERGED = -6,  /* device: reconstruction hit max_steps while still changing */
+    GEO_ERR_WORKSPACE = -7       /* caller-provided workspace too small */
+} geo_status;
+
+/* Human-readable name of a geo_status value (static string). */
+GEO_API const char *geo_status_string(int status);
+
+/*
+ * Reads and clears the device status word of the current device after
+ * synchronising `stream`. *status receives GEO_OK or the first device-side
+ * error (GEO_ERR_TIMEOUT, GEO_ERR_NOT_CONVERGED) recorded since the last
+ * read. Returns GEO_ERR_CUDA if the synchronisation itself failed.
+ */
+GEO_API int geo_device_status(void *stream, int *status);
+
+/*
+ * Geodesic dilation of size `steps` (Eq. 4 with the dilation step of Eq. 3's
+ * dual): out = delta^mask_steps(marker), each step f' = min(delta_1(f), mask).
+ * steps >= 0 (0 copies marker to out). conn is 4 or 8. mask must not be NULL.
+ */
+GEO_API int geo_dilate_chain(geo_dtype dtype, const void *marker, const void *mask, void *out,
+                     int64_t height, int64_t width, int64_t pitch, int conn,
+                     int64_t steps, void *stream);
+
+/* Geodesic erosion of size `steps` (Eq. 3-4): each step f' = max(eps_1(f), mask). */
+GEO_API int geo_erode_chain(geo_dtype dtype, const void *marker, const void *mask, void *out,
+                    int64_t height, int64_t width, int64_t pitch, int conn,
+                    int64_t steps, void *stream);
+
+/*
+ * Reconstruction (Eq. 5): op = 0 dilation by reconstruction delta^mask_rec,
+ * op = 1 erosion by reconstruction eps^mask_rec. Steps are applied until a
+ * step changes no pixel. The device loop runs whole passes of several steps,
+ * so it may apply a few steps past the fixed point; those change nothing.
+ * max_steps caps the number of steps (<= 0: height * width + 1, an upper
+ * bound on the changing steps of any input); hitting the cap while still
+ * changing records GEO_ERR_NOT_CONVERGED in the device status word (the
+ * image reached so far is left in out).
+ * steps_out: optional DEVICE int64_t*; receives the number of steps applied
+ * (an upper bound on the changing steps, rounded up to whole passes).
+ */
+GEO_API int geo_reconstruct(geo_dtype dtype, const void *marker, const void *mask, void *out,
+                    int64_t height, int64_t width, int64_t pitch, int conn, int op,
+                    int64_t max_steps, int64_t *steps_out, void *stream);
+
+/*
+ * Dilation (Eq. 2) / erosion (Eq. 1) by the clipped square window of half
+ * size half_size >= 0, i.e. a (2s+1) x (2s+1) window, computed as half_size
+ * unmasked 8-connected 3x3 steps. out may alias in.
+ */
+GEO_API int morph_window_dilate(geo_dtype dtype, const void *in, void *out, int64_t height,
+                        int64_t width, int64_t pitch, int64_t half_size, void *stream);
+GEO_API int morph_window_erode(geo_dtype dtype, const void *in, void *out, int64_t height,
+                       int64_t width, int64_t pitch, int64_t half_size, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GEOMORPH_H */

@@ -1,0 +1,197 @@
+"""geomorph: geodesic 3x3 chains on one GB300 (sm_103a), Python binding.
+
+This module only marshals arguments: it takes torch CUDA tensors (device
+memory and the current stream), passes their raw pointers to the C ABI of
+libgeomorph.so (declared in include/geomorph.h) through ctypes, and raises
+GeoError on a non-zero status. Every step of the computation runs in the
+library's CUDA kernels; there is no CPU path. If the library is missing it
+is built from csrc/ with nvcc, and if that is impossible the call fails.
+
+Operations (Zlaus & Mongus, IEEE TPDS 2019, Section 2):
+  dilate_chain / erode_chain   Eq. 3-4, `steps` elementary geodesic steps
+  reconstruct                  Eq. 5, iterate until a step changes nothing
+  window_dilate / window_erode Eq. 1-2, clipped (2s+1)^2 square window
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+__all__ = [
+    "GeoError", "load", "library_path", "dilate_chain", "erode_chain", "reconstruct",
+    "window_dilate", "window_erode", "device_status", "DTYPES",
+]
+
+GEO_U8, GEO_F32, GEO_F64 = 0, 1, 2
+DTYPES = {torch.uint8: GEO_U8, torch.float32: GEO_F32, torch.float64: GEO_F64}
+STATUS = {
+    0: "GEO_OK", -1: "GEO_ERR_ARG", -2: "GEO_ERR_DTYPE", -3: "GEO_ERR_ALIGN", -4: "GEO_ERR_CUDA",
+    -5: "GEO_ERR_TIMEOUT", -6: "GEO_ERR_NOT_CONVERGED", -7: "GEO_ERR_WORKSPACE",
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GeoError(RuntimeError):
+    """A geomorph call returned a non-zero geo_status."""
+
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libgeomorph.so (building it with nvcc first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        P, I, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        lib.geo_status_string.argtypes = [I]
+        lib.geo_status_string.restype = ctypes.c_char_p
+        lib.geo_device_status.argtypes = [P, ctypes.POINTER(I)]
+        lib.geo_device_status.restype = I
+        for name in ("geo_dilate_chain", "geo_erode_chain"):
+            fn = getattr(lib, name)
+            fn.argtypes = [I, P, P, P, L, L, L, I, L, P]
+            fn.restype = I
+        lib.geo_reconstruct.argtypes = [I, P, P, P, L, L, L, I, I, L, P, P]
+        lib.geo_reconstruct.restype = I
+        for name in ("morph_window_dilate", "morph_window_erode"):
+            fn = getattr(lib, name)
+            fn.argtypes = [I, P, P, L, L, L, L, P]
+            fn.restype = I
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise GeoError(rc, where)
+
+
+def _stream(t: torch.Tensor) -> int:
+    return torch.cuda.current_stream(t.device).cuda_stream
+
+
+def _image(t: torch.Tensor, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dim() != 2:
+        raise ValueError(f"{name} must be 2-D (height, width), got shape {tuple(t.shape)}")
+    if t.dtype not in DTYPES:
+        raise TypeError(f"{name}: unsupported dtype {t.dtype} (uint8, float32, float64)")
+    if t.shape[1] > 1 and t.stride(1) != 1:
+        raise ValueError(f"{name} rows must be contiguous (stride(1) == 1)")
+    return t
+
+
+def _pitch(t: torch.Tensor) -> int:
+    return max(int(t.stride(0)), int(t.shape[1])) if t.shape[0] > 1 else int(t.shape[1])
+
+
+def _same(a: torch.Tensor, b: torch.Tensor, what: str):
+    if a.shape != b.shape or a.dtype != b.dtype or a.device != b.device:
+        raise ValueError(f"{what}: shape/dtype/device mismatch {tuple(a.shape)} {a.dtype} vs {tuple(b.shape)} {b.dtype}")
+    if a.shape[0] > 1 and _pitch(a) != _pitch(b):
+        raise ValueError(f"{what}: all images of a call share one row pitch")
+
+
+def _out_like(marker: torch.Tensor, out):
+    if out is None:
+        return torch.empty_like(marker, memory_format=torch.contiguous_format) if _pitch(marker) == marker.shape[1] \
+            else torch.empty_strided(marker.shape, marker.stride(), dtype=marker.dtype, device=marker.device)
+    _image(out, "out")
+    _same(marker, out, "out")
+    return out
+
+
+def _chain(name: str, marker, mask, steps: int, conn: int, out):
+    lib = load()
+    _image(marker, "marker")
+    _image(mask, "mask")
+    _same(marker, mask, "mask")
+    out = _out_like(marker, out)
+    H, W = marker.shape
+    with torch.cuda.device(marker.device):
+        rc = getattr(lib, name)(DTYPES[marker.dtype], marker.data_ptr(), mask.data_ptr(), out.data_ptr(),
+                                H, W, _pitch(marker), int(conn), int(steps), _stream(marker))
+    _check(rc, name)
+    return out
+
+
+def dilate_chain(marker: torch.Tensor, mask: torch.Tensor, steps: int, conn: int = 8, out=None) -> torch.Tensor:
+    """`steps` geodesic dilation steps f <- min(delta_1(f), mask) (Eq. 3-4)."""
+    return _chain("geo_dilate_chain", marker, mask, steps, conn, out)
+
+
+def erode_chain(marker: torch.Tensor, mask: torch.Tensor, steps: int, conn: int = 8, out=None) -> torch.Tensor:
+    """`steps` geodesic erosion steps f <- max(eps_1(f), mask) (Eq. 3-4)."""
+    return _chain("geo_erode_chain", marker, mask, steps, conn, out)
+
+
+def reconstruct(marker: torch.Tensor, mask: torch.Tensor, conn: int = 8, op: str = "dilate",
+                max_steps: int = 0, out=None, return_steps: bool = False):
+    """Dilation (op='dilate') or erosion (op='erode') by reconstruction (Eq. 5).
+
+    Device-side non-convergence is recorded in the device status word; call
+    device_status() (it synchronises) to read it.
+    """
+    lib = load()
+    _image(marker, "marker")
+    _image(mask, "mask")
+    _same(marker, mask, "mask")
+    out = _out_like(marker, out)
+    H, W = marker.shape
+    steps = torch.zeros(1, dtype=torch.int64, device=marker.device) if return_steps else None
+    with torch.cuda.device(marker.device):
+        rc = lib.geo_reconstruct(DTYPES[marker.dtype], marker.data_ptr(), mask.data_ptr(), out.data_ptr(),
+                                 H, W, _pitch(marker), int(conn), {"dilate": 0, "erode": 1}[op], int(max_steps),
+                                 None if steps is None else steps.data_ptr(), _stream(marker))
+    _check(rc, "geo_reconstruct")
+    return (out, steps) if return_steps else out
+
+
+def _window(name: str, img, half_size: int, out):
+    lib = load()
+    _image(img, "in")
+    out = _out_like(img, out)
+    H, W = img.shape
+    with torch.cuda.device(img.device):
+        rc = getattr(lib, name)(DTYPES[img.dtype], img.data_ptr(), out.data_ptr(), H, W, _pitch(img),
+                                int(half_size), _stream(img))
+    _check(rc, name)
+    return out
+
+
+def window_dilate(img: torch.Tensor, half_size: int, out=None) -> torch.Tensor:
+    """Dilation by the clipped (2s+1)^2 square (Eq. 2), as s unmasked 3x3 steps."""
+    return _window("morph_window_dilate", img, half_size, out)
+
+
+def window_erode(img: torch.Tensor, half_size: int, out=None) -> torch.Tensor:
+    """Erosion by the clipped (2s+1)^2 square (Eq. 1), as s unmasked 3x3 steps."""
+    return _window("morph_window_erode", img, half_size, out)
+
+
+def device_status(device=None) -> int:
+    """Synchronise the current stream and read-and-clear the device status word."""
+    lib = load()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    with torch.cuda.device(dev):
+        v = ctypes.c_int(0)
+        rc = lib.geo_device_status(torch.cuda.current_stream(dev).cuda_stream, ctypes.byref(v))
+    _check(rc, "geo_device_status")
+    return int(v.value)

@@ -1,0 +1,330 @@
+// extern "C" entry points of libgeomorph.so: argument checks, tile planning,
+// scratch management, launch. Declarations and contracts: include/geomorph.h.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include "geo_common.cuh"
+
+namespace geo {
+
+// ---------------------------------------------------------------------------
+// per-device state: status word and a scratch memory pool
+// ---------------------------------------------------------------------------
+
+constexpr int kMaxDevices = 64;
+
+struct DeviceState {
+  bool init = false;
+  int *status = nullptr;        // sticky device-side error word
+  cudaMemPool_t pool = nullptr;  // library-owned stream-ordered pool
+  int nsm = 0;
+};
+
+static std::mutex g_mu;
+static DeviceState g_dev[kMaxDevices];
+
+static int device_state(DeviceState **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GEO_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  DeviceState &d = g_dev[dev];
+  if (!d.init) {
+    if (cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GEO_ERR_CUDA;
+    if (cudaMalloc(&d.status, sizeof(int)) != cudaSuccess) return GEO_ERR_CUDA;
+    if (cudaMemset(d.status, 0, sizeof(int)) != cudaSuccess) return GEO_ERR_CUDA;
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&d.pool, &props) != cudaSuccess) return GEO_ERR_CUDA;
+    uint64_t thr = UINT64_MAX;  // keep freed scratch cached in the pool
+    cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    d.init = true;
+  }
+  *out = &d;
+  return GEO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// planning
+// ---------------------------------------------------------------------------
+
+struct Plan {
+  int TH, TW, K, rs, tiles_x, tiles_y, grid;
+  size_t smem;
+};
+
+static int elem_size(int dt) { return dt == GEO_U8 ? 1 : dt == GEO_F32 ? 4 : 8; }
+static int chunk_elems(int dt) { return dt == GEO_U8 ? 8 : dt == GEO_F32 ? 4 : 2; }
+
+static int occupancy(int dt, int op, int conn, size_t smem, int *bps) {
+  if (dt == GEO_U8) return occupancy_tile_u8(op, conn, smem, bps);
+  if (dt == GEO_F32) return occupancy_tile_f32(op, conn, smem, bps);
+  return occupancy_tile_f64(op, conn, smem, bps);
+}
+
+static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Choose the tile interior TH x TW and halo K. The cost model per step is
+// (waves of tiles) x (area a tile computes per step, about (TH+K)(TW+K)),
+// plus a fixed synchronisation cost per pass spread over the pass's K steps.
+static int make_plan_uncached(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm,
+                              Plan *P) {
+  const int CE = chunk_elems(dt);
+  int Kmax = dt == GEO_U8 ? 24 : dt == GEO_F32 ? 12 : 6;
+  if (const char *e = getenv("GEOMORPH_K")) Kmax = atoi(e);
+  int K = Kmax;
+  if (steps_hint > 0 && steps_hint < K) K = (int)steps_hint;
+  K = ((K + CE - 1) / CE) * CE;
+  if (K < CE) K = CE;
+  const int SS = dt == GEO_U8 ? 2 : elem_size(dt);
+  const double sync_px = 6000.0;  // barrier cost per pass, in pixel-steps of one SM
+  double best = 1e300;
+  Plan bp{};
+  static const int cand_th[] = {16, 24, 32, 40, 48, 56, 64, 72, 80, 88, 96, 112, 128, 160, 192, 256};
+  static const int cand_tw[] = {16, 24, 32, 40, 48, 56, 64, 72, 80, 88, 96, 112, 128, 160, 192, 256};
+  for (int th : cand_th) {
+    for (int tw : cand_tw) {
+      if (tw % CE) continue;
+      const int RH = th + 2 * K;
+      const int NC = (tw + 2 * K) / CE + 2;
+      int rs = NC * 16;
+      if (rs % 128 == 0) rs += 16;
+      const size_t smem = (size_t)3 * RH * rs;
+      if (smem > 200 * 1024) continue;
+      int bps = 0;
+      if (occupancy(dt, op, conn, smem, &bps) != GEO_OK) return GEO_ERR_CUDA;
+      if (bps <= 0) continue;
+      const int64_t tiles = cdiv(H, th) * cdiv(W, tw);
+      const int64_t slots = (int64_t)bps * nsm;
+      const int64_t grid = tiles < slots ? tiles : slots;
+      // tiles share an SM when more than one CTA is resident per SM
+      const double per_sm = (double)cdiv(tiles, nsm);
+      const double area = (double)(th + K) * (double)(tw + K) * SS;
+      const double cost = per_sm * area + sync_px * SS / K;
+      if (cost < best) {
+        best = cost;
+        bp.TH = th;
+        bp.TW = tw;
+        bp.K = K;
+        bp.rs = rs;
+        bp.tiles_x = (int)cdiv(W, tw);
+        bp.tiles_y = (int)cdiv(H, th);
+        bp.grid = (int)grid;
+        bp.smem = smem;
+      }
+    }
+  }
+  if (best >= 1e300) return GEO_ERR_CUDA;
+  if (const char *e = getenv("GEOMORPH_TILE")) {  // "THxTW" override for tuning sweeps
+    int th = 0, tw = 0;
+    if (sscanf(e, "%dx%d", &th, &tw) == 2 && th > 0 && tw > 0 && tw % CE == 0) {
+      const int RH = th + 2 * K;
+      const int NC = (tw + 2 * K) / CE + 2;
+      int rs = NC * 16;
+      if (rs % 128 == 0) rs += 16;
+      const size_t smem = (size_t)3 * RH * rs;
+      int bps = 0;
+      if (smem <= 227 * 1024 && occupancy(dt, op, conn, smem, &bps) == GEO_OK && bps > 0) {
+        const int64_t tiles = cdiv(H, th) * cdiv(W, tw);
+        const int64_t slots = (int64_t)bps * nsm;
+        bp = Plan{th, tw, K, rs, (int)cdiv(W, tw), (int)cdiv(H, th), (int)(tiles < slots ? tiles : slots), smem};
+      }
+    }
+  }
+  *P = bp;
+  return GEO_OK;
+}
+
+using PlanKey = std::tuple<int, int, int, int, int64_t, int64_t, int64_t, int, std::string, std::string>;
+static std::map<PlanKey, Plan> g_plans;
+static std::mutex g_plan_mu;
+
+static int make_plan(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const char *ek = getenv("GEOMORPH_K");
+  const char *et = getenv("GEOMORPH_TILE");
+  PlanKey key{dev, dt, op, conn, H, W, steps_hint < 64 ? steps_hint : 64, nsm, ek ? ek : "", et ? et : ""};
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto it = g_plans.find(key);
+    if (it != g_plans.end()) {
+      *P = it->second;
+      return GEO_OK;
+    }
+  }
+  int rc = make_plan_uncached(dt, op, conn, H, W, steps_hint, nsm, P);
+  if (rc == GEO_OK) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans[key] = *P;
+  }
+  return rc;
+}
+
+static int launch(int dt, const TileLaunch &L, int op, int conn, cudaStream_t s, const Plan &P) {
+  if (dt == GEO_U8) return launch_tile_u8(L, op, conn, s, P.grid, P.smem);
+  if (dt == GEO_F32) return launch_tile_f32(L, op, conn, s, P.grid, P.smem);
+  return launch_tile_f64(L, op, conn, s, P.grid, P.smem);
+}
+
+static bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+static Plane make_plane(const void *p, int64_t pitch_b, int dt) {
+  const size_t va = dt == GEO_U8 ? 8 : 16;  // width of the kernel's vector access
+  Plane q;
+  q.ptr = (char *)p;
+  q.pitch_b = pitch_b;
+  q.vec_ok = (p != nullptr && aligned(p, va) && pitch_b % (int64_t)va == 0) ? 1 : 0;
+  return q;
+}
+
+static bool overlaps(const void *a, const void *b, size_t n) {
+  const char *x = (const char *)a, *y = (const char *)b;
+  return x < y + n && y < x + n;
+}
+
+// Common driver of chains, reconstruction and windows.
+static int run(int dt, const void *marker, const void *mask, void *out, int64_t H, int64_t W, int64_t pitch,
+               int conn, int op, int mode, int64_t steps, int64_t *steps_out, void *stream) {
+  if (dt != GEO_U8 && dt != GEO_F32 && dt != GEO_F64) return GEO_ERR_DTYPE;
+  if (H < 0 || W < 0 || pitch < W || (conn != 4 && conn != 8) || (op != DILATE && op != ERODE))
+    return GEO_ERR_ARG;
+  if (H == 0 || W == 0) return GEO_OK;
+  if (!marker || !out) return GEO_ERR_ARG;
+  const int es = elem_size(dt);
+  if (!aligned(marker, es) || !aligned(out, es) || (mask && !aligned(mask, es))) return GEO_ERR_ALIGN;
+  const int64_t pitch_b = pitch * es;
+  const size_t span = (size_t)((H - 1) * pitch_b + W * es);
+  if (mask && overlaps(mask, out, span)) return GEO_ERR_ARG;
+  const bool alias = (marker == out);
+  if (!alias && overlaps(marker, out, span)) return GEO_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  if (mode == MODE_CHAIN && steps == 0) {
+    if (alias) return GEO_OK;
+    return cudaMemcpy2DAsync(out, pitch_b, marker, pitch_b, W * es, H, cudaMemcpyDeviceToDevice, s) == cudaSuccess
+               ? GEO_OK
+               : GEO_ERR_CUDA;
+  }
+
+  DeviceState *ds = nullptr;
+  int rc = device_state(&ds);
+  if (rc != GEO_OK) return rc;
+  Plan P;
+  rc = make_plan(dt, op, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P);
+  if (rc != GEO_OK) return rc;
+
+  // scratch: control words + one ping-pong image with a 16-byte aligned pitch
+  const int64_t spitch_b = ((W * es + 15) / 16) * 16;
+  const size_t ctl_b = 256;
+  const size_t scratch_b = ctl_b + (size_t)spitch_b * (size_t)H;
+  void *scratch = nullptr;
+  if (cudaMallocFromPoolAsync(&scratch, scratch_b, ds->pool, s) != cudaSuccess) return GEO_ERR_CUDA;
+  rc = GEO_OK;
+  if (cudaMemsetAsync(scratch, 0, ctl_b, s) != cudaSuccess) rc = GEO_ERR_CUDA;
+
+  TileLaunch L;
+  memset(&L, 0, sizeof(L));
+  L.marker = make_plane(marker, pitch_b, dt);
+  L.mask = make_plane(mask, pitch_b, dt);
+  L.out = make_plane(out, pitch_b, dt);
+  L.scratch = make_plane((char *)scratch + ctl_b, spitch_b, dt);
+  L.H = H;
+  L.W = W;
+  L.TH = P.TH;
+  L.TW = P.TW;
+  L.K = P.K;
+  L.tiles_x = P.tiles_x;
+  L.tiles_y = P.tiles_y;
+  L.rs = P.rs;
+  L.mode = mode;
+  L.steps = steps;
+  L.alias = alias ? 1 : 0;
+  L.ctl = (Control *)scratch;
+  L.status = ds->status;
+  L.steps_out = steps_out;
+  if (mode == MODE_CHAIN) {
+    int64_t np = cdiv(steps, P.K);
+    if (alias && (np & 1)) ++np;  // pass 0 must not write the buffer it reads
+    L.npasses = (int)np;
+  }
+  if (rc == GEO_OK) rc = launch(dt, L, op, conn, s, P);
+  if (cudaFreeAsync(scratch, s) != cudaSuccess && rc == GEO_OK) rc = GEO_ERR_CUDA;
+  return rc;
+}
+
+}  // namespace geo
+
+using namespace geo;
+
+extern "C" {
+
+const char *geo_status_string(int status) {
+  switch (status) {
+    case GEO_OK: return "GEO_OK";
+    case GEO_ERR_ARG: return "GEO_ERR_ARG: invalid argument";
+    case GEO_ERR_DTYPE: return "GEO_ERR_DTYPE: unsupported element type";
+    case GEO_ERR_ALIGN: return "GEO_ERR_ALIGN: misaligned pointer";
+    case GEO_ERR_CUDA: return "GEO_ERR_CUDA: CUDA runtime error";
+    case GEO_ERR_TIMEOUT: return "GEO_ERR_TIMEOUT: device wait expired";
+    case GEO_ERR_NOT_CONVERGED: return "GEO_ERR_NOT_CONVERGED: reconstruction hit max_steps";
+    case GEO_ERR_WORKSPACE: return "GEO_ERR_WORKSPACE: workspace too small";
+    default: return "unknown geo_status";
+  }
+}
+
+int geo_device_status(void *stream, int *status) {
+  if (!status) return GEO_ERR_ARG;
+  DeviceState *ds = nullptr;
+  int rc = device_state(&ds);
+  if (rc != GEO_OK) return rc;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return GEO_ERR_CUDA;
+  int v = 0;
+  if (cudaMemcpy(&v, ds->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GEO_ERR_CUDA;
+  if (cudaMemset(ds->status, 0, sizeof(int)) != cudaSuccess) return GEO_ERR_CUDA;
+  *status = v;
+  return GEO_OK;
+}
+
+int geo_dilate_chain(geo_dtype dtype, const void *marker, const void *mask, void *out, int64_t height,
+                     int64_t width, int64_t pitch, int conn, int64_t steps, void *stream) {
+  if (steps < 0 || (!mask && height > 0 && width > 0)) return GEO_ERR_ARG;
+  return run(dtype, marker, mask, out, height, width, pitch, conn, DILATE, MODE_CHAIN, steps, nullptr, stream);
+}
+
+int geo_erode_chain(geo_dtype dtype, const void *marker, const void *mask, void *out, int64_t height,
+                    int64_t width, int64_t pitch, int conn, int64_t steps, void *stream) {
+  if (steps < 0 || (!mask && height > 0 && width > 0)) return GEO_ERR_ARG;
+  return run(dtype, marker, mask, out, height, width, pitch, conn, ERODE, MODE_CHAIN, steps, nullptr, stream);
+}
+
+int geo_reconstruct(geo_dtype dtype, const void *marker, const void *mask, void *out, int64_t height,
+                    int64_t width, int64_t pitch, int conn, int op, int64_t max_steps, int64_t *steps_out,
+                    void *stream) {
+  if (op != 0 && op != 1) return GEO_ERR_ARG;
+  if (!mask && height > 0 && width > 0) return GEO_ERR_ARG;
+  if (max_steps <= 0) max_steps = height * width + 1;
+  return run(dtype, marker, mask, out, height, width, pitch, conn, op, MODE_REC, max_steps, steps_out, stream);
+}
+
+int morph_window_dilate(geo_dtype dtype, const void *in, void *out, int64_t height, int64_t width, int64_t pitch,
+                        int64_t half_size, void *stream) {
+  if (half_size < 0) return GEO_ERR_ARG;
+  return run(dtype, in, nullptr, out, height, width, pitch, 8, DILATE, MODE_CHAIN, half_size, nullptr, stream);
+}
+
+int morph_window_erode(geo_dtype dtype, const void *in, void *out, int64_t height, int64_t width, int64_t pitch,
+                       int64_t half_size, void *stream) {
+  if (half_size < 0) return GEO_ERR_ARG;
+  return run(dtype, in, nullptr, out, height, width, pitch, 8, ERODE, MODE_CHAIN, half_size, nullptr, stream);
+}
+
+}  // extern "C"

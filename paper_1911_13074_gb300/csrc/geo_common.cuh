@@ -1,0 +1,62 @@
+// Shared device/host definitions of the geomorph CUDA library (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/geomorph.h"
+
+namespace geo {
+
+enum Op : int { DILATE = 0, ERODE = 1 };
+enum Mode : int { MODE_CHAIN = 0, MODE_REC = 1 };
+
+constexpr int kThreads = 256;  // threads per CTA of the tile kernels
+
+// One image operand of a pass: base pointer, row stride in bytes, and
+// whether 16-byte vector access is legal (base and stride 16-byte aligned).
+struct Plane {
+  char *ptr;
+  int64_t pitch_b;
+  int vec_ok;
+};
+
+// Inter-CTA control words, zeroed by the host before each launch.
+struct Control {
+  unsigned int bar_count;  // grid barrier arrivals
+  unsigned int bar_gen;    // grid barrier generation
+  int flags[3];            // per-pass "changed" flags (rotating)
+  int pad;
+};
+
+struct TileLaunch {
+  Plane marker;   // input of pass 0
+  Plane mask;     // mask (ptr == nullptr: unmasked window, virtual mask)
+  Plane out;      // caller's output
+  Plane scratch;  // library scratch (ping-pong partner of out)
+  int64_t H, W;
+  int TH, TW, K;          // tile interior (px) and halo (px)
+  int tiles_x, tiles_y;
+  int rs;                 // shared-memory row stride in bytes
+  int mode;               // MODE_CHAIN or MODE_REC
+  int npasses;            // chain: number of passes
+  int64_t steps;          // chain: total steps; rec: max steps
+  int alias;              // rec: 1 if out aliases marker
+  Control *ctl;
+  int *status;            // per-device sticky status word
+  int64_t *steps_out;     // rec: optional device pointer
+};
+
+// Host-side launcher per element type (defined in geo_tile_<dtype>.cu).
+struct LaunchConfig {
+  int TH, TW, K;
+};
+
+int launch_tile_u8(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid, size_t smem);
+int launch_tile_f32(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid, size_t smem);
+int launch_tile_f64(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid, size_t smem);
+int occupancy_tile_u8(int op, int conn, size_t smem, int *blocks_per_sm);
+int occupancy_tile_f32(int op, int conn, size_t smem, int *blocks_per_sm);
+int occupancy_tile_f64(int op, int conn, size_t smem, int *blocks_per_sm);
+
+}  // namespace geo

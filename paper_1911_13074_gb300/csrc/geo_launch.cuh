@@ -1,0 +1,35 @@
+// Host-side launch of the tile kernel for one element type (included once per
+// element-type translation unit so the three instantiations compile in parallel).
+#pragma once
+
+#include "geo_tile.cuh"
+
+namespace geo {
+
+template <template <int> class EP>
+static void *tile_kernel_ptr(int op, int conn) {
+  if (op == DILATE) return conn == 8 ? (void *)tile_kernel<EP<DILATE>, 8> : (void *)tile_kernel<EP<DILATE>, 4>;
+  return conn == 8 ? (void *)tile_kernel<EP<ERODE>, 8> : (void *)tile_kernel<EP<ERODE>, 4>;
+}
+
+template <template <int> class EP>
+static int launch_tile_impl(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid, size_t smem) {
+  void *k = tile_kernel_ptr<EP>(op, conn);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return GEO_ERR_CUDA;
+  TileLaunch arg = L;
+  void *args[] = {(void *)&arg};
+  cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kThreads), args, smem, s);
+  return e == cudaSuccess ? GEO_OK : GEO_ERR_CUDA;
+}
+
+template <template <int> class EP>
+static int occupancy_impl(int op, int conn, size_t smem, int *bps) {
+  void *k = tile_kernel_ptr<EP>(op, conn);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return GEO_ERR_CUDA;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, kThreads, smem) == cudaSuccess ? GEO_OK
+                                                                                                : GEO_ERR_CUDA;
+}
+
+}  // namespace geo

@@ -1,0 +1,12 @@
+// Tile-kernel instantiations for u8 images.
+#include "geo_launch.cuh"
+
+namespace geo {
+
+int launch_tile_u8(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid, size_t smem) {
+  return launch_tile_impl<EU8>(L, op, conn, s, grid, smem);
+}
+
+int occupancy_tile_u8(int op, int conn, size_t smem, int *bps) { return occupancy_impl<EU8>(op, conn, smem, bps); }
+
+}  // namespace geo

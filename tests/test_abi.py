@@ -1,0 +1,62 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads,
+and exports every function that include/geomorph.h declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = "\n".join(l for l in src.splitlines() if not l.lstrip().startswith("#"))
+        names += re.findall(r"GEO_API\s+[\w\s\*]*?\b(\w+)\s*\(", src)
+    return names
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for required in ("geo_dilate_chain", "geo_erode_chain", "geo_reconstruct", "morph_window_dilate",
+                     "morph_window_erode", "geo_status_string", "geo_device_status"):
+        assert required in names
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    from paper_1911_13074_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_status_strings():
+    import paper_1911_13074_gb300 as gm
+    lib = gm.load()
+    assert lib.geo_status_string(0) == b"GEO_OK"
+    for code in range(-7, 0):
+        assert lib.geo_status_string(code).startswith(b"GEO_ERR_")
+
+
+def test_host_argument_checks_need_no_device():
+    """Calls rejected on the host return their status before touching the GPU."""
+    import paper_1911_13074_gb300 as gm
+    lib = gm.load()
+    # bad dtype, bad connectivity, pitch < width, negative steps
+    assert lib.geo_dilate_chain(7, 16, 16, 16, 4, 4, 4, 8, 3, None) == -2
+    assert lib.geo_dilate_chain(0, 16, 16, 16, 4, 4, 4, 6, 3, None) == -1
+    assert lib.geo_dilate_chain(0, 16, 16, 16, 4, 4, 3, 8, 3, None) == -1
+    assert lib.geo_erode_chain(0, 16, 16, 16, 4, 4, 4, 8, -1, None) == -1
+    assert lib.morph_window_dilate(1, 16, 32, 4, 4, 4, -2, None) == -1
+    assert lib.geo_reconstruct(0, 16, 16, 16, 4, 4, 4, 8, 3, 0, None, None) == -1
+    # empty images are a no-op
+    assert lib.geo_dilate_chain(0, None, None, None, 0, 5, 5, 8, 3, None) == 0
+    assert lib.morph_window_erode(2, None, None, 3, 0, 0, 4, None) == 0
+    # misaligned float pointer, mask overlapping out
+    assert lib.geo_dilate_chain(1, 18, 64, 128, 2, 2, 2, 8, 1, None) == -3
+    assert lib.geo_dilate_chain(0, 0x1000, 0x2000, 0x2000, 2, 2, 2, 8, 1, None) == -1

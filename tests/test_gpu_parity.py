@@ -1,0 +1,157 @@
+"""GPU parity: the CUDA library against the CPU oracle, element by element.
+
+Forward results only select among input values, so the bar is bit-exact
+equality in every dtype. Inputs are seeded (synth/); expected values come
+from the oracle only. Shapes span several tiles with ragged tails, single
+rows and columns, and step counts around the pass length.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def gm():
+    import paper_1911_13074_gb300 as m
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rand_pair(H, W, kind, rng, op="dilate"):
+    if kind == "u8":
+        m = rng.integers(0, 256, (H, W)).astype(np.uint8)
+        d = rng.integers(0, 80, (H, W))
+        f = np.clip(m.astype(np.int64) + (d if op == "erode" else -d), 0, 255).astype(np.uint8)
+    else:
+        dt = np.float32 if kind == "f32" else np.float64
+        m = rng.standard_normal((H, W)).astype(dt)
+        d = np.abs(rng.standard_normal((H, W))).astype(dt)
+        f = (m + d if op == "erode" else m - d).astype(dt)
+    return f, m
+
+
+def assert_same(got, ref, what=""):
+    if not np.array_equal(got, ref):
+        bad = np.argwhere(got != ref)
+        y, x = bad[0]
+        raise AssertionError(f"{what}: {len(bad)} mismatches, first at ({y},{x}): gpu={got[y, x]} oracle={ref[y, x]}")
+
+
+SHAPES = [(1, 1), (1, 37), (29, 1), (3, 5), (17, 33), (64, 64), (100, 77), (129, 257), (250, 190)]
+
+
+@pytest.mark.parametrize("kind", ["u8", "f32", "f64"])
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+@pytest.mark.parametrize("conn", [4, 8])
+def test_chain_parity_shapes_and_lengths(kind, op, conn):
+    rng = np.random.default_rng(hash((kind, op, conn)) % 2**32)
+    m = gm()
+    fn = m.dilate_chain if op == "dilate" else m.erode_chain
+    for H, W in SHAPES:
+        f, msk = rand_pair(H, W, kind, rng, op)
+        for steps in (0, 1, 2, 5, 11, 12, 13, 23, 24, 25, 60):
+            got = host(fn(dev(f), dev(msk), steps, conn=conn))
+            ref = oracle.chain(f, msk, steps, conn=conn, op=op)
+            assert_same(got, ref, f"{kind} {op} conn{conn} {H}x{W} steps={steps}")
+    assert m.device_status() == 0
+
+
+@pytest.mark.parametrize("kind", ["u8", "f32", "f64"])
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+def test_window_parity(kind, op):
+    rng = np.random.default_rng(7)
+    m = gm()
+    fn = m.window_dilate if op == "dilate" else m.window_erode
+    for H, W in [(1, 1), (7, 300), (300, 7), (131, 203)]:
+        img = rand_pair(H, W, kind, rng)[1]
+        for s in (0, 1, 4, 13, 40):
+            got = host(fn(dev(img), s))
+            assert_same(got, oracle.window(img, s, op), f"window {kind} {op} {H}x{W} s={s}")
+
+
+@pytest.mark.parametrize("kind", ["u8", "f32", "f64"])
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+@pytest.mark.parametrize("conn", [4, 8])
+def test_reconstruct_parity(kind, op, conn):
+    rng = np.random.default_rng(11 + conn)
+    m = gm()
+    for H, W in [(1, 1), (1, 50), (40, 1), (45, 61), (150, 170)]:
+        f, msk = rand_pair(H, W, kind, rng, op)
+        out, steps = m.reconstruct(dev(f), dev(msk), conn=conn, op=op, return_steps=True)
+        ref, n = oracle.reconstruct(f, msk, conn=conn, op=op)
+        assert_same(host(out), ref, f"rec {kind} {op} conn{conn} {H}x{W}")
+        assert int(steps.item()) >= n
+    assert m.device_status() == 0
+
+
+def test_workload0_chain_and_reconstruction():
+    """256x256 u8: 64-step 8-connected dilation chain, then reconstruction to stability."""
+    w = synth.workload0()
+    m = gm()
+    f, msk = dev(w["marker"]), dev(w["mask"])
+    assert_same(host(m.dilate_chain(f, msk, 64)), oracle.chain(w["marker"], w["mask"], 64), "chain64")
+    rec, steps = m.reconstruct(f, msk, return_steps=True)
+    ref, n = oracle.reconstruct(w["marker"], w["mask"])
+    assert_same(host(rec), ref, "reconstruction")
+    assert n > 0 and int(steps.item()) >= n
+    assert m.device_status() == 0
+
+
+@pytest.mark.parametrize("kind", ["u8", "f32", "f64"])
+def test_in_place_and_strided(kind):
+    rng = np.random.default_rng(3)
+    m = gm()
+    f, msk = rand_pair(90, 130, kind, rng)
+    ref = oracle.chain(f, msk, 37)
+    # in place: out aliases marker (odd and even pass counts)
+    for steps in (37, 24, 1):
+        t = dev(f)
+        m.dilate_chain(t, dev(msk), steps, out=t)
+        assert_same(host(t), oracle.chain(f, msk, steps), f"in-place {kind} steps={steps}")
+    # row pitch larger than the width, odd (scalar path) and 16-byte multiple (vector path)
+    for extra in (3, 16):
+        big_f = dev(np.zeros((90, 130 + extra), f.dtype))
+        big_m = dev(np.zeros((90, 130 + extra), f.dtype))
+        big_o = dev(np.zeros((90, 130 + extra), f.dtype))
+        vf, vm, vo = big_f[:, 5:135], big_m[:, 5:135], big_o[:, 5:135]
+        vf.copy_(dev(f))
+        vm.copy_(dev(msk))
+        m.dilate_chain(vf, vm, 37, out=vo)
+        assert_same(host(vo).copy(), ref, f"strided {kind} extra={extra}")
+        # pixels outside the view are untouched
+        assert np.all(host(big_o)[:, :5] == 0) and np.all(host(big_o)[:, 135:] == 0)
+
+
+def test_reconstruct_not_converged_status():
+    w = synth.workload0(64, 64)
+    m = gm()
+    m.reconstruct(dev(w["marker"]), dev(w["mask"]), max_steps=3)
+    assert m.device_status() == -6
+    assert m.device_status() == 0  # read clears
+
+
+def test_full_size_1024_u8_chain_sampled():
+    """1024x1024 u8, 1500-step chains: the oracle is run on a 1500-step chain
+    restricted to the window that determines a sample of output rows
+    (a pixel's value after N steps depends only on pixels within N of it)."""
+    w = synth.workload1_u8()
+    m = gm()
+    for op, key in (("dilate", "marker_dilate"), ("erode", "marker_erode")):
+        fn = m.dilate_chain if op == "dilate" else m.erode_chain
+        got = host(fn(dev(w[key]), dev(w["mask"]), 100, conn=8))
+        # full image for 100 steps
+        assert_same(got, oracle.chain(w[key], w["mask"], 100, conn=8, op=op), f"1024 {op} 100")
