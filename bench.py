@@ -1,0 +1,292 @@
+"""Benchmark: geodesic 3x3 dilation chains on one GB300 (or N replicas).
+
+A bench step is one 1500-step, 8-connected geodesic dilation chain
+(f <- min(delta_1(f), mask), Zlaus & Mongus Eq. 3-4) on a 1024x1024 uint8
+marker/mask pair from the seeded synthetic generator, through the C ABI
+entry point geo_dilate_chain. The metric is Gpixel-steps/s =
+H * W * chain_steps / seconds / 1e9, summed over all ranks (replicas).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (the plain C loops of oracle/) on the
+host cores instead, on a bounded number of chain steps per bench step.
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H = W = 1024
+CHAIN_STEPS = 1500
+CONN = 8
+OPS_PER_PX_STEP = 5  # 8-connected masked step: 2 row + 2 column extremes + 1 mask clamp
+WORKLOAD = "1024x1024 uint8 8-connected geodesic dilation chain, 1500 steps (synthetic workload 1)"
+METRIC = "Gpixel-steps/s (1024² u8, 1500-step geodesic chain)"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="geomorph", choices=["geomorph", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_setup(n):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def alu_peak_top_s(nsm, mhz):
+    """Peak exact min/max rate for uint8 pixels, in tera pixel-ops per second.
+
+    The fastest exact primitive for uint8 values on sm_103a is max.u16x2 /
+    min.u16x2: 128 lanes per clock per SM, each lane deciding two pixels.
+    """
+    return nsm * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def run_reference(args, rank, world):
+    """CPU oracle, timed on the host cores on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    import synth
+    w = synth.workload1_u8(H, W)
+    f, m = w["marker_dilate"], w["mask"]
+    sample_steps = 20  # chain steps per bench step (the full 1500 would take about a minute)
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.chain(f, m, sample_steps, conn=CONN)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.chain(f, m, sample_steps, conn=CONN)
+    dt = time.perf_counter() - t0
+    value = H * W * sample_steps * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gpixel-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "H": H, "W": W, "chain_steps_timed_per_step": sample_steps,
+                   "conn": CONN},
+        "cpu_baseline": {"value": value, "unit": "Gpixel-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"1024x1024 u8 8-connected dilation chain, {sample_steps} steps per bench step"},
+        "e2e": {"value": value, "unit": "Gpixel-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline():
+    """The oracle as it stands, single thread, on a bounded sample (~10 s)."""
+    import oracle
+    import synth
+    w = synth.workload1_u8(H, W)
+    f, m = w["marker_dilate"], w["mask"]
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.chain(f, m, 5, conn=CONN)
+    per_step = (time.perf_counter() - t0) / 5
+    n = max(5, min(400, int(10.0 / max(per_step, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.chain(f, m, n, conn=CONN)
+    dt = time.perf_counter() - t0
+    return {"value": H * W * n / dt / 1e9, "unit": "Gpixel-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"1024x1024 u8 8-connected dilation chain, {n} of the 1500 steps, {dt:.1f} s"}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    import paper_1911_13074_gb300 as gm
+    import synth
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = synth.workload1_u8(H, W)
+    marker_h = torch.from_numpy(w["marker_dilate"]).pin_memory()
+    mask_h = torch.from_numpy(w["mask"]).pin_memory()
+    marker = marker_h.to(dev)
+    mask = mask_h.to(dev)
+    out = torch.empty_like(marker)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        gm.dilate_chain(marker, mask, CHAIN_STEPS, conn=CONN, out=out)
+    torch.cuda.synchronize(dev)
+    if gm.device_status() != 0:
+        raise RuntimeError("device status error during warm-up")
+
+    # device-timed region: inputs resident, L2 flushed between timed chains
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        gm.dilate_chain(marker, mask, CHAIN_STEPS, conn=CONN, out=out)
+        ev[i][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    per = [a.elapsed_time(b) for a, b in ev]  # ms
+    t_dev = sum(per) / 1e3
+    status = gm.device_status()
+    if status != 0:
+        raise RuntimeError(f"device status {status}")
+
+    # end to end through the public API with host buffers
+    out_h = torch.empty_like(marker_h).pin_memory()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        mk = marker_h.to(dev, non_blocking=True)
+        ms = mask_h.to(dev, non_blocking=True)
+        gm.dilate_chain(mk, ms, CHAIN_STEPS, conn=CONN, out=out)
+        out_h.copy_(out, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    t_e2e = e0.elapsed_time(e1) / 1e3
+
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev, t_e2e = float(tt[0]), float(tt[1])
+    if rank != 0:
+        return
+
+    px_steps = H * W * CHAIN_STEPS
+    value = world * px_steps * args.steps / t_dev / 1e9
+    e2e_value = world * px_steps * args.steps / t_e2e / 1e9
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
+    peak = alu_peak_top_s(nsm, sm_max)
+    per_launch_s = statistics.mean(per) / 1e3
+    achieved = px_steps * OPS_PER_PX_STEP / per_launch_s / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gpixel-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "H": H, "W": W, "chain_steps": CHAIN_STEPS, "conn": CONN,
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "flushed between timed chains (256 MiB write, outside the events)"},
+        "fps": args.steps / t_dev,
+        "wall_s_timed_region": t_wall,
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": "Gpixel-steps/s", "h2d_bytes_per_step": 2 * H * W,
+                "d2h_bytes_per_step": H * W},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tpixel-op/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_basis": f"{nsm} SMs x 128 lanes/clk x 2 px (max.u16x2) x {sm_max:.0f} MHz",
+                     "ops_per_pixel_step": OPS_PER_PX_STEP},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -162,6 +162,9 @@ static int make_plan(int dt, int op, int conn, int64_t H, int64_t W, int64_t ste
     }
   }
   int rc = make_plan_uncached(dt, op, conn, H, W, steps_hint, nsm, P);
+  if (rc == GEO_OK && getenv("GEOMORPH_DEBUG"))
+    fprintf(stderr, "geomorph plan: dt=%d op=%d conn=%d %lldx%lld -> tile %dx%d K=%d tiles=%dx%d grid=%d smem=%zu\n",
+            dt, op, conn, (long long)H, (long long)W, P->TH, P->TW, P->K, P->tiles_y, P->tiles_x, P->grid, P->smem);
   if (rc == GEO_OK) {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     g_plans[key] = *P;

@@ -124,9 +124,9 @@ def test_in_place_and_strided(kind):
         assert_same(host(t), oracle.chain(f, msk, steps), f"in-place {kind} steps={steps}")
     # row pitch larger than the width, odd (scalar path) and 16-byte multiple (vector path)
     for extra in (3, 16):
-        big_f = dev(np.zeros((90, 130 + extra), f.dtype))
-        big_m = dev(np.zeros((90, 130 + extra), f.dtype))
-        big_o = dev(np.zeros((90, 130 + extra), f.dtype))
+        big_f = dev(np.zeros((90, 135 + extra), f.dtype))
+        big_m = dev(np.zeros((90, 135 + extra), f.dtype))
+        big_o = dev(np.zeros((90, 135 + extra), f.dtype))
         vf, vm, vo = big_f[:, 5:135], big_m[:, 5:135], big_o[:, 5:135]
         vf.copy_(dev(f))
         vm.copy_(dev(msk))
