@@ -125,6 +125,28 @@ GEO_API int morph_window_dilate(geo_dtype dtype, const void *in, void *out, int6
 GEO_API int morph_window_erode(geo_dtype dtype, const void *in, void *out, int64_t height,
                        int64_t width, int64_t pitch, int64_t half_size, void *stream);
 
+/*
+ * geo_dilate_chain without any memory allocation. The paper has no
+ * counterpart; this exists for callers that cannot allocate GPU memory during
+ * a call (a fixed memory budget owned by another allocator, a real-time loop
+ * that must not reach the driver's allocator, device memory reserved up
+ * front). Same arguments and result as geo_dilate_chain; its scratch image is
+ * a static device array of 16 MiB that every GPU loading the library holds
+ * until the process exits.
+ *   - Images whose scratch, round_up(width * element_size, 16) * height bytes,
+ *     exceeds 16 MiB are rejected with GEO_ERR_WORKSPACE (4096 x 4096 uint8,
+ *     2048 x 2048 float32 and 1448 x 1448 float64 fit).
+ *   - All calls share the one array: calls that overlap on the GPU race and
+ *     corrupt each other's output; the caller must order them.
+ *   - The first call on a device sets up that device (looks up the array's
+ *     device address and plans the tiles); make it before any stream capture.
+ *   - A device-side wait that expires leaves out incomplete; it is not
+ *     reported through geo_device_status.
+ */
+GEO_API int geo_dilate_chain_noalloc(geo_dtype dtype, const void *marker, const void *mask, void *out,
+                             int64_t height, int64_t width, int64_t pitch, int conn,
+                             int64_t steps, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

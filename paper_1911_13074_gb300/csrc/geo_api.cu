@@ -56,11 +56,6 @@ static int device_state(DeviceState **out) {
 // planning
 // ---------------------------------------------------------------------------
 
-struct Plan {
-  int TH, TW, K, rs, tiles_x, tiles_y, grid;
-  size_t smem;
-};
-
 static int elem_size(int dt) { return dt == GEO_U8 ? 1 : dt == GEO_F32 ? 4 : 8; }
 static int chunk_elems(int dt) { return dt == GEO_U8 ? 8 : dt == GEO_F32 ? 4 : 2; }
 
@@ -75,8 +70,7 @@ static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // Choose the tile interior TH x TW and halo K. The cost model per step is
 // (waves of tiles) x (area a tile computes per step, about (TH+K)(TW+K)),
 // plus a fixed synchronisation cost per pass spread over the pass's K steps.
-static int make_plan_uncached(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm,
-                              Plan *P) {
+int plan_tiles(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P) {
   const int CE = chunk_elems(dt);
   int Kmax = dt == GEO_U8 ? 24 : dt == GEO_F32 ? 12 : 6;
   if (const char *e = getenv("GEOMORPH_K")) Kmax = atoi(e);
@@ -161,7 +155,7 @@ static int make_plan(int dt, int op, int conn, int64_t H, int64_t W, int64_t ste
       return GEO_OK;
     }
   }
-  int rc = make_plan_uncached(dt, op, conn, H, W, steps_hint, nsm, P);
+  int rc = plan_tiles(dt, op, conn, H, W, steps_hint, nsm, P);
   if (rc == GEO_OK && getenv("GEOMORPH_DEBUG"))
     fprintf(stderr, "geomorph plan: dt=%d op=%d conn=%d %lldx%lld -> tile %dx%d K=%d tiles=%dx%d grid=%d smem=%zu\n",
             dt, op, conn, (long long)H, (long long)W, P->TH, P->TW, P->K, P->tiles_y, P->tiles_x, P->grid, P->smem);
@@ -172,7 +166,7 @@ static int make_plan(int dt, int op, int conn, int64_t H, int64_t W, int64_t ste
   return rc;
 }
 
-static int launch(int dt, const TileLaunch &L, int op, int conn, cudaStream_t s, const Plan &P) {
+int launch_plan(int dt, const TileLaunch &L, int op, int conn, cudaStream_t s, const Plan &P) {
   if (dt == GEO_U8) return launch_tile_u8(L, op, conn, s, P.grid, P.smem);
   if (dt == GEO_F32) return launch_tile_f32(L, op, conn, s, P.grid, P.smem);
   return launch_tile_f64(L, op, conn, s, P.grid, P.smem);
@@ -259,7 +253,7 @@ static int run(int dt, const void *marker, const void *mask, void *out, int64_t 
     if (alias && (np & 1)) ++np;  // pass 0 must not write the buffer it reads
     L.npasses = (int)np;
   }
-  if (rc == GEO_OK) rc = launch(dt, L, op, conn, s, P);
+  if (rc == GEO_OK) rc = launch_plan(dt, L, op, conn, s, P);
   if (cudaFreeAsync(scratch, s) != cudaSuccess && rc == GEO_OK) rc = GEO_ERR_CUDA;
   return rc;
 }

@@ -47,10 +47,18 @@ struct TileLaunch {
   int64_t *steps_out;     // rec: optional device pointer
 };
 
-// Host-side launcher per element type (defined in geo_tile_<dtype>.cu).
-struct LaunchConfig {
-  int TH, TW, K;
+// Tile geometry of one launch: interior TH x TW, halo K, shared-memory row
+// stride rs, tile grid, CTA count and dynamic shared memory.
+struct Plan {
+  int TH, TW, K, rs, tiles_x, tiles_y, grid;
+  size_t smem;
 };
+
+// Uncached tile planning and launch (geo_api.cu).
+int plan_tiles(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P);
+int launch_plan(int dt, const TileLaunch &L, int op, int conn, cudaStream_t s, const Plan &P);
+
+// Host-side launcher per element type (defined in geo_tile_<dtype>.cu).
 
 int launch_tile_u8(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid, size_t smem);
 int launch_tile_f32(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid, size_t smem);
