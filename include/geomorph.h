@@ -104,10 +104,12 @@ GEO_API int geo_erode_chain(geo_dtype dtype, const void *marker, const void *mas
  * op = 1 erosion by reconstruction eps^mask_rec. Steps are applied until a
  * step changes no pixel. The device loop runs whole passes of several steps,
  * so it may apply a few steps past the fixed point; those change nothing.
- * max_steps caps the number of steps (<= 0: height * width + 1, an upper
- * bound on the changing steps of any input); hitting the cap while still
- * changing records GEO_ERR_NOT_CONVERGED in the device status word (the
- * image reached so far is left in out).
+ * max_steps caps the number of steps applied, counted in whole passes
+ * (<= 0: height * width + 1 + 1024, which covers the changing steps of any
+ * input, at most height * width + 1, plus the pass that detects the fixed
+ * point); a pass that reaches the cap and still changed a pixel records
+ * GEO_ERR_NOT_CONVERGED in the device status word (the image reached so far
+ * is left in out).
  * steps_out: optional DEVICE int64_t*; receives the number of steps applied
  * (an upper bound on the changing steps, rounded up to whole passes).
  */

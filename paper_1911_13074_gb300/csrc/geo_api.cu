@@ -166,6 +166,101 @@ static int make_plan(int dt, int op, int conn, int64_t H, int64_t W, int64_t ste
   return rc;
 }
 
+// ---------------------------------------------------------------------------
+// register-resident kernel: fixed region per element type, K chosen here
+// ---------------------------------------------------------------------------
+
+struct RRGeom {
+  int CW, RW, NW, B;
+};
+// must match RU8 / RF32 / RF64 in geo_rr.cuh
+static RRGeom rr_geom(int dt) {
+  if (dt == GEO_U8) return RRGeom{4, 8, 8, 2};
+  if (dt == GEO_F32) return RRGeom{4, 16, 8, 1};
+  return RRGeom{2, 16, 8, 1};
+}
+
+static int occupancy_rr(int dt, int op, int conn, int *bps) {
+  if (dt == GEO_U8) return occupancy_rr_u8(op, conn, bps);
+  if (dt == GEO_F32) return occupancy_rr_f32(op, conn, bps);
+  return occupancy_rr_f64(op, conn, bps);
+}
+
+// Pick the halo K of the register-resident kernel. Cost model in units of
+// one region-step (one step of one CTA on its whole region): a pass costs
+// kSyncSteps for its load / store / grid barrier, and every step costs one
+// unit per tile an SM has to process in that pass.
+static int plan_rr_uncached(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P) {
+  const RRGeom g = rr_geom(dt);
+  const int RWID = 32 * g.CW, RHGT = g.NW * g.RW * g.B;
+  int bps = 0;
+  if (occupancy_rr(dt, op, conn, &bps) != GEO_OK || bps <= 0) return GEO_ERR_CUDA;
+  double kSyncSteps = 10.0;
+  if (const char *e = getenv("GEOMORPH_SYNC")) kSyncSteps = atof(e);
+  int forceK = 0;
+  if (const char *e = getenv("GEOMORPH_K")) forceK = atoi(e);
+  double best = 1e300;
+  Plan bp{};
+  const int kmax = (RWID < RHGT ? RWID : RHGT) / 2 - g.CW;
+  for (int K = g.CW; K <= kmax; K += g.CW) {
+    if (forceK > 0 && K != ((forceK + g.CW - 1) / g.CW) * g.CW) continue;
+    const int TW = RWID - 2 * K, TH = RHGT - 2 * K;
+    const int64_t tiles = cdiv(H, TH) * cdiv(W, TW);
+    const double per_sm = (double)cdiv(tiles, nsm);
+    double cost;
+    if (steps_hint > 0) {
+      const double passes = (double)cdiv(steps_hint, K);
+      cost = passes * kSyncSteps * per_sm + per_sm * (double)steps_hint;
+    } else {
+      // reconstruction: the step count is unknown; take the longest side as
+      // its scale and charge the overshoot (the pass that ends past the fixed
+      // point and the pass that detects it, about 1.5 K steps)
+      const double n = (double)(H > W ? H : W);
+      cost = per_sm * (n + 1.5 * K) + (n / K + 2.0) * kSyncSteps * per_sm;
+    }
+    if (cost < best) {
+      best = cost;
+      const int64_t slots = (int64_t)bps * nsm;
+      bp = Plan{TH, TW, K, 0, (int)cdiv(W, TW), (int)cdiv(H, TH), (int)(tiles < slots ? tiles : slots), 0};
+    }
+  }
+  if (best >= 1e300) return GEO_ERR_ARG;
+  *P = bp;
+  return GEO_OK;
+}
+
+static int make_plan_rr(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const char *ek = getenv("GEOMORPH_K");
+  const char *es = getenv("GEOMORPH_SYNC");
+  PlanKey key{dev, dt + 16, op, conn, H, W, steps_hint, nsm, ek ? ek : "", es ? es : ""};
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto it = g_plans.find(key);
+    if (it != g_plans.end()) {
+      *P = it->second;
+      return GEO_OK;
+    }
+  }
+  int rc = plan_rr_uncached(dt, op, conn, H, W, steps_hint, nsm, P);
+  if (rc == GEO_OK && getenv("GEOMORPH_DEBUG"))
+    fprintf(stderr, "geomorph rr plan: dt=%d op=%d conn=%d %lldx%lld steps=%lld -> interior %dx%d K=%d tiles=%dx%d grid=%d\n",
+            dt, op, conn, (long long)H, (long long)W, (long long)steps_hint, P->TH, P->TW, P->K, P->tiles_y,
+            P->tiles_x, P->grid);
+  if (rc == GEO_OK) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans[key] = *P;
+  }
+  return rc;
+}
+
+static int launch_rr(int dt, const TileLaunch &L, int op, int conn, cudaStream_t s, const Plan &P) {
+  if (dt == GEO_U8) return launch_rr_u8(L, op, conn, s, P.grid);
+  if (dt == GEO_F32) return launch_rr_f32(L, op, conn, s, P.grid);
+  return launch_rr_f64(L, op, conn, s, P.grid);
+}
+
 int launch_plan(int dt, const TileLaunch &L, int op, int conn, cudaStream_t s, const Plan &P) {
   if (dt == GEO_U8) return launch_tile_u8(L, op, conn, s, P.grid, P.smem);
   if (dt == GEO_F32) return launch_tile_f32(L, op, conn, s, P.grid, P.smem);
@@ -174,8 +269,10 @@ int launch_plan(int dt, const TileLaunch &L, int op, int conn, cudaStream_t s, c
 
 static bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-static Plane make_plane(const void *p, int64_t pitch_b, int dt) {
-  const size_t va = dt == GEO_U8 ? 8 : 16;  // width of the kernel's vector access
+static Plane make_plane(const void *p, int64_t pitch_b, int dt, bool rr) {
+  // width of the kernel's vector access: 16-byte chunks (8 bytes for u8) in
+  // the shared-memory kernel, CW pixels per lane in the register kernel
+  const size_t va = rr ? (size_t)rr_geom(dt).CW * elem_size(dt) : (dt == GEO_U8 ? 8 : 16);
   Plane q;
   q.ptr = (char *)p;
   q.pitch_b = pitch_b;
@@ -215,8 +312,11 @@ static int run(int dt, const void *marker, const void *mask, void *out, int64_t 
   DeviceState *ds = nullptr;
   int rc = device_state(&ds);
   if (rc != GEO_OK) return rc;
+  const char *kern = getenv("GEOMORPH_KERNEL");
+  const bool rr = !(kern && strcmp(kern, "tile") == 0);
   Plan P;
-  rc = make_plan(dt, op, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P);
+  rc = rr ? make_plan_rr(dt, op, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P)
+          : make_plan(dt, op, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P);
   if (rc != GEO_OK) return rc;
 
   // scratch: control words + one ping-pong image with a 16-byte aligned pitch
@@ -230,10 +330,10 @@ static int run(int dt, const void *marker, const void *mask, void *out, int64_t 
 
   TileLaunch L;
   memset(&L, 0, sizeof(L));
-  L.marker = make_plane(marker, pitch_b, dt);
-  L.mask = make_plane(mask, pitch_b, dt);
-  L.out = make_plane(out, pitch_b, dt);
-  L.scratch = make_plane((char *)scratch + ctl_b, spitch_b, dt);
+  L.marker = make_plane(marker, pitch_b, dt, rr);
+  L.mask = make_plane(mask, pitch_b, dt, rr);
+  L.out = make_plane(out, pitch_b, dt, rr);
+  L.scratch = make_plane((char *)scratch + ctl_b, spitch_b, dt, rr);
   L.H = H;
   L.W = W;
   L.TH = P.TH;
@@ -253,7 +353,7 @@ static int run(int dt, const void *marker, const void *mask, void *out, int64_t 
     if (alias && (np & 1)) ++np;  // pass 0 must not write the buffer it reads
     L.npasses = (int)np;
   }
-  if (rc == GEO_OK) rc = launch_plan(dt, L, op, conn, s, P);
+  if (rc == GEO_OK) rc = rr ? launch_rr(dt, L, op, conn, s, P) : launch_plan(dt, L, op, conn, s, P);
   if (cudaFreeAsync(scratch, s) != cudaSuccess && rc == GEO_OK) rc = GEO_ERR_CUDA;
   return rc;
 }
@@ -308,7 +408,9 @@ int geo_reconstruct(geo_dtype dtype, const void *marker, const void *mask, void 
                     void *stream) {
   if (op != 0 && op != 1) return GEO_ERR_ARG;
   if (!mask && height > 0 && width > 0) return GEO_ERR_ARG;
-  if (max_steps <= 0) max_steps = height * width + 1;
+  // default cap: every changing step of any input (at most H*W + 1) plus room
+  // for the last, unchanged pass that detects the fixed point (K <= 1024)
+  if (max_steps <= 0) max_steps = height * width + 1 + 1024;
   return run(dtype, marker, mask, out, height, width, pitch, conn, op, MODE_REC, max_steps, steps_out, stream);
 }
 

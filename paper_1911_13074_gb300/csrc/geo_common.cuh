@@ -63,6 +63,12 @@ int launch_plan(int dt, const TileLaunch &L, int op, int conn, cudaStream_t s, c
 int launch_tile_u8(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid, size_t smem);
 int launch_tile_f32(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid, size_t smem);
 int launch_tile_f64(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid, size_t smem);
+int launch_rr_u8(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid);
+int launch_rr_f32(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid);
+int launch_rr_f64(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid);
+int occupancy_rr_u8(int op, int conn, int *blocks_per_sm);
+int occupancy_rr_f32(int op, int conn, int *blocks_per_sm);
+int occupancy_rr_f64(int op, int conn, int *blocks_per_sm);
 int occupancy_tile_u8(int op, int conn, size_t smem, int *blocks_per_sm);
 int occupancy_tile_f32(int op, int conn, size_t smem, int *blocks_per_sm);
 int occupancy_tile_f64(int op, int conn, size_t smem, int *blocks_per_sm);

@@ -2,6 +2,7 @@
 // element-type translation unit so the three instantiations compile in parallel).
 #pragma once
 
+#include "geo_rr.cuh"
 #include "geo_tile.cuh"
 
 namespace geo {
@@ -30,6 +31,28 @@ static int occupancy_impl(int op, int conn, size_t smem, int *bps) {
     return GEO_ERR_CUDA;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, kThreads, smem) == cudaSuccess ? GEO_OK
                                                                                                 : GEO_ERR_CUDA;
+}
+
+template <template <int> class RP>
+static void *rr_kernel_ptr(int op, int conn) {
+  if (op == DILATE) return conn == 8 ? (void *)rr_kernel<RP<DILATE>, 8> : (void *)rr_kernel<RP<DILATE>, 4>;
+  return conn == 8 ? (void *)rr_kernel<RP<ERODE>, 8> : (void *)rr_kernel<RP<ERODE>, 4>;
+}
+
+template <template <int> class RP>
+static int launch_rr_impl(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid) {
+  void *k = rr_kernel_ptr<RP>(op, conn);
+  TileLaunch arg = L;
+  void *args[] = {(void *)&arg};
+  cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(grid), dim3(RP<DILATE>::NW * 32), args, 0, s);
+  return e == cudaSuccess ? GEO_OK : GEO_ERR_CUDA;
+}
+
+template <template <int> class RP>
+static int occupancy_rr_impl(int op, int conn, int *bps) {
+  void *k = rr_kernel_ptr<RP>(op, conn);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, RP<DILATE>::NW * 32, 0) == cudaSuccess ? GEO_OK
+                                                                                                      : GEO_ERR_CUDA;
 }
 
 }  // namespace geo

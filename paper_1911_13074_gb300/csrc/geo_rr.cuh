@@ -1,0 +1,475 @@
+// Register-resident, temporally blocked kernel for geodesic 3x3 chains.
+//
+// Same pass structure as the shared-memory tile kernel (geo_tile.cuh): one
+// cooperative persistent launch per chain (Eq. 4) or reconstruction (Eq. 5),
+// K steps per pass on a tile plus a K-pixel halo, grid barrier between
+// passes, per-pass "changed" flag for reconstruction. What differs is where
+// the tile lives during the K steps: in registers.
+//
+//   * A CTA holds a region of (32 * CW) x (NW * PH) pixels: warp w owns a
+//     horizontal band of PH pixel rows, lane l owns CW adjacent columns of it.
+//   * Horizontal neighbours inside a lane are in the lane's own registers;
+//     the two at the lane's edges come from the adjacent lanes by __shfl.
+//   * Vertical neighbours inside a warp's band are in the lane's registers;
+//     the rows just above and below the band come from the adjacent warps
+//     through a small shared-memory exchange, once per step (one barrier).
+//   * uint8 pixels are "sliced": a 32-bit word holds the pixels of one column
+//     at rows r and r + RW of the band as two u16 lanes, so one max.u16x2
+//     decides two pixels and no byte shifts are needed except at the seam
+//     between the two halves of the band (one funnel shift per column).
+//   * The step itself is Section 3.1's decomposition: row 3-extreme (h),
+//     column 3-extreme of h (8-conn) or of {f above, h, f below} (4-conn),
+//     then the mask clamp of Eq. 3, computed in place top to bottom with the
+//     h rows of the previous and next row kept in registers (the GPU
+//     counterpart of Algorithm 3's two row caches).
+//
+// The region edges that have no neighbour (lanes 0 and 31, warps 0 and
+// NW-1) read stale or identity values; that error moves inward one pixel per
+// step and never reaches the tile interior, which is K pixels in.
+#pragma once
+
+#include "geo_tile.cuh"
+
+namespace geo {
+
+// ---------------------------------------------------------------------------
+// register-resident element policies
+// ---------------------------------------------------------------------------
+
+template <int OP>
+struct RU8 {
+  using Wd = uint32_t;  // two u16 lanes: rows r and r + RW of one column
+  using Px = uint32_t;  // one pixel value (0..255)
+  using G = uint8_t;
+  static constexpr int BANDS = 2, CW = 4, RW = 4, NW = 16, GS = 1;
+  __device__ static Wd e2(Wd a, Wd b) { return OP == DILATE ? umax2(a, b) : umin2(a, b); }
+  __device__ static Wd ext3(Wd a, Wd b, Wd c) { return e2(e2(a, b), c); }
+  __device__ static Wd clamp(Wd v, Wd m) { return OP == DILATE ? umin2(v, m) : umax2(v, m); }
+  __device__ static Px ident() { return OP == DILATE ? 0u : 255u; }
+  __device__ static Px anti() { return OP == DILATE ? 255u : 0u; }
+  __device__ static Wd identw() { return ident() * 0x00010001u; }
+  __device__ static Wd make(Px lo, Px hi) { return lo | (hi << 16); }
+  __device__ static Px get(Wd w, int band) { return band ? (w >> 16) : (w & 0xffffu); }
+  // word holding the pixels just above the band's two halves: the row above
+  // the band (high lane of the upper warp's last word) and row RW-1 (low lane
+  // of the own last word)
+  __device__ static Wd up(Wd above, Wd own_last) { return __funnelshift_l(above, own_last, 16); }
+  // word holding the pixels just below: row RW (high lane of own first word)
+  // and the row below the band (low lane of the lower warp's first word)
+  __device__ static Wd down(Wd own_first, Wd below) { return __funnelshift_r(own_first, below, 16); }
+  __device__ static Px to_px(G g) { return g; }
+  __device__ static G from_px(Px p) { return (G)p; }
+  __device__ static uint4 pack(const Wd (&v)[CW]) { return make_uint4(v[0], v[1], v[2], v[3]); }
+  __device__ static void unpack(uint4 u, Wd (&v)[CW]) {
+    v[0] = u.x;
+    v[1] = u.y;
+    v[2] = u.z;
+    v[3] = u.w;
+  }
+  // CW = 4 consecutive pixels from global memory (one 4-byte access)
+  __device__ static void load_vec(const char *p, bool cg, Px (&v)[CW]) {
+    const uint32_t x = cg ? __ldcg(reinterpret_cast<const unsigned int *>(p))
+                          : __ldg(reinterpret_cast<const unsigned int *>(p));
+    v[0] = x & 0xffu;
+    v[1] = (x >> 8) & 0xffu;
+    v[2] = (x >> 16) & 0xffu;
+    v[3] = x >> 24;
+  }
+  __device__ static void store_vec(char *p, const Px (&v)[CW]) {
+    __stcg(reinterpret_cast<unsigned int *>(p), v[0] | (v[1] << 8) | (v[2] << 16) | (v[3] << 24));
+  }
+  __device__ static bool differs_vec(const char *p, const Px (&v)[CW]) {
+    return __ldcg(reinterpret_cast<const unsigned int *>(p)) != (v[0] | (v[1] << 8) | (v[2] << 16) | (v[3] << 24));
+  }
+};
+
+template <int OP>
+struct RF32 {
+  using Wd = float;
+  using Px = float;
+  using G = float;
+  static constexpr int BANDS = 1, CW = 4, RW = 8, NW = 16, GS = 4;
+  __device__ static Wd e2(Wd a, Wd b) { return OP == DILATE ? fmaxf(a, b) : fminf(a, b); }
+  __device__ static Wd ext3(Wd a, Wd b, Wd c) { return OP == DILATE ? fmax3(a, b, c) : fmin3(a, b, c); }
+  __device__ static Wd clamp(Wd v, Wd m) { return OP == DILATE ? fminf(v, m) : fmaxf(v, m); }
+  __device__ static Px ident() { return OP == DILATE ? -__int_as_float(0x7f800000) : __int_as_float(0x7f800000); }
+  __device__ static Px anti() { return OP == DILATE ? __int_as_float(0x7f800000) : -__int_as_float(0x7f800000); }
+  __device__ static Wd identw() { return ident(); }
+  __device__ static Wd make(Px lo, Px) { return lo; }
+  __device__ static Px get(Wd w, int) { return w; }
+  __device__ static Wd up(Wd above, Wd) { return above; }
+  __device__ static Wd down(Wd, Wd below) { return below; }
+  __device__ static Px to_px(G g) { return g; }
+  __device__ static G from_px(Px p) { return p; }
+  __device__ static uint4 pack(const Wd (&v)[CW]) {
+    return make_uint4(__float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]), __float_as_uint(v[3]));
+  }
+  __device__ static void unpack(uint4 u, Wd (&v)[CW]) {
+    v[0] = __uint_as_float(u.x);
+    v[1] = __uint_as_float(u.y);
+    v[2] = __uint_as_float(u.z);
+    v[3] = __uint_as_float(u.w);
+  }
+  __device__ static void load_vec(const char *p, bool cg, Px (&v)[CW]) {
+    const float4 x = cg ? __ldcg(reinterpret_cast<const float4 *>(p)) : __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = x.z;
+    v[3] = x.w;
+  }
+  __device__ static void store_vec(char *p, const Px (&v)[CW]) {
+    __stcg(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+  }
+  __device__ static bool differs_vec(const char *p, const Px (&v)[CW]) {
+    const uint4 o = __ldcg(reinterpret_cast<const uint4 *>(p));
+    return (o.x != __float_as_uint(v[0])) | (o.y != __float_as_uint(v[1])) | (o.z != __float_as_uint(v[2])) |
+           (o.w != __float_as_uint(v[3]));
+  }
+};
+
+template <int OP>
+struct RF64 {
+  using Wd = long long;  // order-preserving key of the double
+  using Px = long long;
+  using G = double;
+  static constexpr int BANDS = 1, CW = 2, RW = 8, NW = 16, GS = 8;
+  __device__ static Wd e2(Wd a, Wd b) { return OP == DILATE ? max(a, b) : min(a, b); }
+  __device__ static Wd ext3(Wd a, Wd b, Wd c) { return e2(e2(a, b), c); }
+  __device__ static Wd clamp(Wd v, Wd m) { return OP == DILATE ? min(v, m) : max(v, m); }
+  __device__ static Px ident() { return OP == DILATE ? (long long)0x8000000000000000ULL : 0x7fffffffffffffffLL; }
+  __device__ static Px anti() { return OP == DILATE ? 0x7fffffffffffffffLL : (long long)0x8000000000000000ULL; }
+  __device__ static Wd identw() { return ident(); }
+  __device__ static Wd make(Px lo, Px) { return lo; }
+  __device__ static Px get(Wd w, int) { return w; }
+  __device__ static Wd up(Wd above, Wd) { return above; }
+  __device__ static Wd down(Wd, Wd below) { return below; }
+  __device__ static Px to_px(G g) { return f64_key(g); }
+  __device__ static G from_px(Px p) { return key_f64(p); }
+  __device__ static uint4 pack(const Wd (&v)[CW]) {
+    return make_uint4((unsigned)v[0], (unsigned)((unsigned long long)v[0] >> 32), (unsigned)v[1],
+                      (unsigned)((unsigned long long)v[1] >> 32));
+  }
+  __device__ static void unpack(uint4 u, Wd (&v)[CW]) {
+    v[0] = (long long)(((unsigned long long)u.y << 32) | u.x);
+    v[1] = (long long)(((unsigned long long)u.w << 32) | u.z);
+  }
+  __device__ static void load_vec(const char *p, bool cg, Px (&v)[CW]) {
+    const longlong2 x =
+        cg ? __ldcg(reinterpret_cast<const longlong2 *>(p)) : __ldg(reinterpret_cast<const longlong2 *>(p));
+    v[0] = f64_key(__longlong_as_double(x.x));
+    v[1] = f64_key(__longlong_as_double(x.y));
+  }
+  __device__ static void store_vec(char *p, const Px (&v)[CW]) {
+    __stcg(reinterpret_cast<longlong2 *>(p),
+           make_longlong2(__double_as_longlong(key_f64(v[0])), __double_as_longlong(key_f64(v[1]))));
+  }
+  __device__ static bool differs_vec(const char *p, const Px (&v)[CW]) {
+    const longlong2 o = __ldcg(reinterpret_cast<const longlong2 *>(p));
+    return (o.x != __double_as_longlong(key_f64(v[0]))) | (o.y != __double_as_longlong(key_f64(v[1])));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// split-phase CTA barrier on an mbarrier in shared memory
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// Wait for the phase with the given parity to complete. Gives up (returns
+// false) after kWaitLimitNs so that a broken arrival count cannot hang the GPU.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  uint32_t done = 0;
+  unsigned n = 0;
+  unsigned long long t0 = 0;
+  for (;;) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (n == 0) t0 = globaltimer_ns();
+    if ((++n & 1023u) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the kernel
+// ---------------------------------------------------------------------------
+
+template <class P>
+struct RR {
+  using Wd = typename P::Wd;
+  using Px = typename P::Px;
+  using G = typename P::G;
+  static constexpr int CW = P::CW, RW = P::RW, NW = P::NW, B = P::BANDS, GS = P::GS;
+  static constexpr int PH = RW * B;     // pixel rows per warp
+  static constexpr int RWID = 32 * CW;  // region width in pixels
+  static constexpr int RHGT = NW * PH;  // region height in pixels
+
+  // CW pixels of global row gy starting at column gx; pixels outside the
+  // image read `fill`. virt: the window's virtual mask instead of plane Q.
+  __device__ static void load_px(const Plane &Q, int64_t H, int64_t W, int64_t gy, int64_t gx, bool cg, bool virt,
+                                 Px (&v)[CW]) {
+    const bool row_in = gy >= 0 && gy < H;
+    if (virt) {
+#pragma unroll
+      for (int c = 0; c < CW; ++c) v[c] = (row_in && gx + c >= 0 && gx + c < W) ? P::anti() : P::ident();
+      return;
+    }
+    if (row_in && gx >= 0 && gx + CW <= W && Q.vec_ok) {
+      P::load_vec(Q.ptr + gy * Q.pitch_b + gx * GS, cg, v);
+      return;
+    }
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+      if (row_in && gx + c >= 0 && gx + c < W) {
+        const G *p = reinterpret_cast<const G *>(Q.ptr + gy * Q.pitch_b + (gx + c) * GS);
+        v[c] = P::to_px(cg ? __ldcg(p) : __ldg(p));
+      } else {
+        v[c] = P::ident();
+      }
+    }
+  }
+
+  __device__ static void load_words(const Plane &Q, int64_t H, int64_t W, int64_t gy0, int64_t gx, bool cg,
+                                    bool virt, Wd (&w)[RW][CW]) {
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+      Px lo[CW], hi[CW];
+      load_px(Q, H, W, gy0 + r, gx, cg, virt, lo);
+      if constexpr (B == 2) {
+        load_px(Q, H, W, gy0 + RW + r, gx, cg, virt, hi);
+      } else {
+#pragma unroll
+        for (int c = 0; c < CW; ++c) hi[c] = lo[c];
+      }
+#pragma unroll
+      for (int c = 0; c < CW; ++c) w[r][c] = P::make(lo[c], hi[c]);
+    }
+  }
+
+  // row 3-extreme of one word row; the lane-edge neighbours come by shuffle
+  __device__ static void hrow(const Wd (&row)[CW], Wd (&h)[CW]) {
+    const Wd left = __shfl_up_sync(0xffffffffu, row[CW - 1], 1);
+    const Wd right = __shfl_down_sync(0xffffffffu, row[0], 1);
+    h[0] = P::ext3(left, row[0], row[1]);
+#pragma unroll
+    for (int c = 1; c < CW - 1; ++c) h[c] = P::ext3(row[c - 1], row[c], row[c + 1]);
+    h[CW - 1] = P::ext3(row[CW - 2], row[CW - 1], right);
+  }
+
+  // One elementary step, in place, on the lane's words. The band's top and
+  // bottom rows are published to the neighbouring warps through xb; the
+  // split-phase barrier `bar` lets the warp update its inner rows (which need
+  // no neighbour data) before it waits for the other warps' rows. Returns
+  // false if that wait expired.
+  template <int CONN>
+  __device__ static bool step(Wd (&w)[RW][CW], const Wd (&m)[RW][CW], Wd *xb, uint64_t *bar, uint32_t parity,
+                              int lane, int warp) {
+    static_assert(RW >= 2, "a band needs distinct first and last word rows");
+    Wd *mine = xb + (size_t)(warp + 1) * 2 * RWID + lane * CW;
+    *reinterpret_cast<uint4 *>(mine) = P::pack(w[0]);
+    *reinterpret_cast<uint4 *>(mine + RWID) = P::pack(w[RW - 1]);
+    mbar_arrive(bar);
+    // row 3-extremes of every old row; old boundary rows; the parts of the
+    // boundary rows' results that need no neighbour-warp data
+    Wd h[RW][CW], first[CW], last[CW], pre0[CW], preL[CW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) hrow(w[r], h[r]);
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+      first[c] = w[0][c];
+      last[c] = w[RW - 1][c];
+      if constexpr (CONN == 8) {
+        pre0[c] = P::e2(h[0][c], h[1][c]);
+        preL[c] = P::e2(h[RW - 2][c], h[RW - 1][c]);
+      } else {
+        pre0[c] = P::e2(h[0][c], w[1][c]);
+        preL[c] = P::e2(w[RW - 2][c], h[RW - 1][c]);
+      }
+    }
+    // inner rows 1 .. RW-2
+    if constexpr (CONN == 8) {
+#pragma unroll
+      for (int r = 1; r < RW - 1; ++r)
+#pragma unroll
+        for (int c = 0; c < CW; ++c) w[r][c] = P::clamp(P::ext3(h[r - 1][c], h[r][c], h[r + 1][c]), m[r][c]);
+    } else {
+      Wd fp[CW];
+#pragma unroll
+      for (int c = 0; c < CW; ++c) fp[c] = first[c];
+#pragma unroll
+      for (int r = 1; r < RW - 1; ++r) {
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+          const Wd old = w[r][c];
+          w[r][c] = P::clamp(P::ext3(fp[c], h[r][c], w[r + 1][c]), m[r][c]);
+          fp[c] = old;
+        }
+      }
+    }
+    const bool ok = mbar_wait(bar, parity);
+    Wd above[CW], below[CW], upw[CW], dnw[CW];
+    P::unpack(*reinterpret_cast<const uint4 *>(xb + (size_t)warp * 2 * RWID + RWID + lane * CW), above);
+    P::unpack(*reinterpret_cast<const uint4 *>(xb + (size_t)(warp + 2) * 2 * RWID + lane * CW), below);
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+      upw[c] = P::up(above[c], last[c]);
+      dnw[c] = P::down(first[c], below[c]);
+    }
+    if constexpr (CONN == 8) {
+      Wd hu[CW], hd[CW];
+      hrow(upw, hu);
+      hrow(dnw, hd);
+#pragma unroll
+      for (int c = 0; c < CW; ++c) {
+        w[0][c] = P::clamp(P::e2(pre0[c], hu[c]), m[0][c]);
+        w[RW - 1][c] = P::clamp(P::e2(preL[c], hd[c]), m[RW - 1][c]);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < CW; ++c) {
+        w[0][c] = P::clamp(P::e2(pre0[c], upw[c]), m[0][c]);
+        w[RW - 1][c] = P::clamp(P::e2(preL[c], dnw[c]), m[RW - 1][c]);
+      }
+    }
+    return ok;
+  }
+
+  // store the interior part of the lane's words to D; with cmp, report
+  // whether any stored pixel differs from plane C (the pass input)
+  __device__ static bool store(const Wd (&w)[RW][CW], const Plane &D, const Plane &C, bool cmp, int64_t H, int64_t W,
+                               int64_t ty0, int64_t tx0, int K, int TH, int TW, int lane, int warp) {
+    const int X = lane * CW;
+    if (X < K || X + CW > K + TW) return false;
+    const int64_t gx = tx0 + (X - K);
+    if (gx >= W) return false;
+    const bool vec = (gx + CW <= W) && D.vec_ok && (!cmp || C.vec_ok);
+    bool changed = false;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+#pragma unroll
+      for (int r = 0; r < RW; ++r) {
+        const int Y = warp * PH + b * RW + r;
+        if (Y < K || Y >= K + TH) continue;
+        const int64_t gy = ty0 + (Y - K);
+        if (gy >= H) continue;
+        Px v[CW];
+#pragma unroll
+        for (int c = 0; c < CW; ++c) v[c] = P::get(w[r][c], b);
+        char *dp = D.ptr + gy * D.pitch_b + gx * GS;
+        const char *cp = C.ptr + gy * C.pitch_b + gx * GS;
+        if (vec) {
+          if (cmp) changed |= P::differs_vec(cp, v);
+          P::store_vec(dp, v);
+        } else {
+#pragma unroll
+          for (int c = 0; c < CW; ++c) {
+            if (gx + c < W) {
+              const G g = P::from_px(v[c]);
+              if (cmp) changed |= (__ldcg(reinterpret_cast<const G *>(cp) + c) != g);
+              __stcg(reinterpret_cast<G *>(dp) + c, g);
+            }
+          }
+        }
+      }
+    }
+    return changed;
+  }
+};
+
+template <class P, int CONN>
+__global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
+  using R = RR<P>;
+  using Wd = typename P::Wd;
+  constexpr int CW = R::CW, RW = R::RW, NW = R::NW, PH = R::PH, RWID = R::RWID;
+  __shared__ __align__(16) Wd xbuf[2][NW + 2][2][RWID];
+  __shared__ int changed_s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int K = L.K, TH = L.TH, TW = L.TW;
+  const int ntiles = L.tiles_x * L.tiles_y;
+  const bool rec = (L.mode == MODE_REC);
+  const bool virt = (L.mask.ptr == nullptr);
+  const bool mask_resident = (ntiles <= (int)gridDim.x);
+
+  __shared__ __align__(8) uint64_t xbar;
+  if (threadIdx.x == 0) mbar_init(&xbar, NW * 32);
+  // the slots above warp 0 and below warp NW-1 hold the identity
+  for (int i = threadIdx.x; i < 2 * 2 * RWID; i += NW * 32) {
+    const int par = i / (2 * RWID), rest = i % (2 * RWID);
+    (&xbuf[par][0][0][0])[rest] = P::identw();
+    (&xbuf[par][NW + 1][0][0])[rest] = P::identw();
+  }
+  __syncthreads();
+
+  Wd w[RW][CW], m[RW][CW];
+  int64_t steps_left = L.steps, steps_done = 0;
+  int parity = 0;
+  for (int pass = 0;; ++pass) {
+    int S;
+    if (!rec) {
+      if (pass >= L.npasses) break;
+      const int64_t base = L.steps / L.npasses, extra = L.steps % L.npasses;
+      S = (int)(base + (pass < extra ? 1 : 0));
+    } else {
+      S = (int)(steps_left < (int64_t)K ? steps_left : (int64_t)K);
+    }
+    const bool to_out = rec ? (((pass + L.alias) & 1) == 0) : (((L.npasses - 1 - pass) & 1) == 0);
+    const Plane dst = to_out ? L.out : L.scratch;
+    const Plane src = (pass == 0) ? L.marker : (to_out ? L.scratch : L.out);
+    const bool src_cg = (pass > 0) || (L.marker.ptr == L.out.ptr);
+
+    if (threadIdx.x == 0) changed_s = 0;
+    bool changed = false;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const int ty = t / L.tiles_x, tx = t - ty * L.tiles_x;
+      const int64_t ty0 = (int64_t)ty * TH, tx0 = (int64_t)tx * TW;
+      const int64_t gy0 = ty0 - K + warp * PH;
+      const int64_t gx = tx0 - K + lane * CW;
+      R::load_words(src, L.H, L.W, gy0, gx, src_cg, false, w);
+      if (!mask_resident || pass == 0) R::load_words(L.mask, L.H, L.W, gy0, gx, false, virt, m);
+      bool ok = true;
+      for (int j = 0; j < S; ++j) {
+        ok &= R::template step<CONN>(w, m, &xbuf[parity][0][0][0], &xbar, parity, lane, warp);
+        parity ^= 1;
+      }
+      if (!ok) record_status(L.status, GEO_ERR_TIMEOUT);
+      changed |= R::store(w, dst, src, rec, L.H, L.W, ty0, tx0, K, TH, TW, lane, warp);
+    }
+    if (rec) {
+      if (changed) changed_s = 1;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        if (changed_s) atomicOr(&L.ctl->flags[pass % 3], 1);
+        if (blockIdx.x == 0) L.ctl->flags[(pass + 1) % 3] = 0;
+      }
+      steps_done += S;
+      steps_left -= S;
+    } else if (pass == L.npasses - 1) {
+      break;
+    }
+    if (!grid_barrier(L.ctl, L.status, gridDim.x)) return;
+    if (rec) {
+      const int f = *(volatile int *)&L.ctl->flags[pass % 3];
+      if (!f) break;
+      if (steps_left <= 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) record_status(L.status, GEO_ERR_NOT_CONVERGED);
+        break;
+      }
+    }
+  }
+  if (rec && L.steps_out && blockIdx.x == 0 && threadIdx.x == 0) *L.steps_out = steps_done;
+}
+
+}  // namespace geo

@@ -9,4 +9,10 @@ int launch_tile_u8(const TileLaunch &L, int op, int conn, cudaStream_t s, int gr
 
 int occupancy_tile_u8(int op, int conn, size_t smem, int *bps) { return occupancy_impl<EU8>(op, conn, smem, bps); }
 
+int launch_rr_u8(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid) {
+  return launch_rr_impl<RU8>(L, op, conn, s, grid);
+}
+
+int occupancy_rr_u8(int op, int conn, int *bps) { return occupancy_rr_impl<RU8>(op, conn, bps); }
+
 }  // namespace geo

@@ -5,6 +5,8 @@ equality in every dtype. Inputs are seeded (synth/); expected values come
 from the oracle only. Shapes span several tiles with ragged tails, single
 rows and columns, and step counts around the pass length.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -20,6 +22,22 @@ DEV = "cuda"
 def gm():
     import paper_1911_13074_gb300 as m
     return m
+
+
+@pytest.fixture(params=["rr", "tile"])
+def kernel(request):
+    """Run a test on the register-resident kernel (default) and on the
+    shared-memory tile kernel (GEOMORPH_KERNEL=tile)."""
+    old = os.environ.get("GEOMORPH_KERNEL")
+    if request.param == "tile":
+        os.environ["GEOMORPH_KERNEL"] = "tile"
+    else:
+        os.environ.pop("GEOMORPH_KERNEL", None)
+    yield request.param
+    if old is None:
+        os.environ.pop("GEOMORPH_KERNEL", None)
+    else:
+        os.environ["GEOMORPH_KERNEL"] = old
 
 
 def dev(a):
@@ -57,13 +75,13 @@ SHAPES = [(1, 1), (1, 37), (29, 1), (3, 5), (17, 33), (64, 64), (100, 77), (129,
 @pytest.mark.parametrize("kind", ["u8", "f32", "f64"])
 @pytest.mark.parametrize("op", ["dilate", "erode"])
 @pytest.mark.parametrize("conn", [4, 8])
-def test_chain_parity_shapes_and_lengths(kind, op, conn):
+def test_chain_parity_shapes_and_lengths(kind, op, conn, kernel):
     rng = np.random.default_rng(hash((kind, op, conn)) % 2**32)
     m = gm()
     fn = m.dilate_chain if op == "dilate" else m.erode_chain
     for H, W in SHAPES:
         f, msk = rand_pair(H, W, kind, rng, op)
-        for steps in (0, 1, 2, 5, 11, 12, 13, 23, 24, 25, 60):
+        for steps in (0, 1, 2, 5, 11, 12, 13, 19, 20, 21, 23, 24, 25, 60):
             got = host(fn(dev(f), dev(msk), steps, conn=conn))
             ref = oracle.chain(f, msk, steps, conn=conn, op=op)
             assert_same(got, ref, f"{kind} {op} conn{conn} {H}x{W} steps={steps}")
@@ -72,7 +90,7 @@ def test_chain_parity_shapes_and_lengths(kind, op, conn):
 
 @pytest.mark.parametrize("kind", ["u8", "f32", "f64"])
 @pytest.mark.parametrize("op", ["dilate", "erode"])
-def test_window_parity(kind, op):
+def test_window_parity(kind, op, kernel):
     rng = np.random.default_rng(7)
     m = gm()
     fn = m.window_dilate if op == "dilate" else m.window_erode
@@ -81,16 +99,18 @@ def test_window_parity(kind, op):
         for s in (0, 1, 4, 13, 40):
             got = host(fn(dev(img), s))
             assert_same(got, oracle.window(img, s, op), f"window {kind} {op} {H}x{W} s={s}")
+            assert m.device_status() == 0, f"device status after window {kind} {op} {H}x{W} s={s}"
 
 
 @pytest.mark.parametrize("kind", ["u8", "f32", "f64"])
 @pytest.mark.parametrize("op", ["dilate", "erode"])
 @pytest.mark.parametrize("conn", [4, 8])
-def test_reconstruct_parity(kind, op, conn):
+def test_reconstruct_parity(kind, op, conn, kernel):
     rng = np.random.default_rng(11 + conn)
     m = gm()
     for H, W in [(1, 1), (1, 50), (40, 1), (45, 61), (150, 170)]:
         f, msk = rand_pair(H, W, kind, rng, op)
+        assert m.device_status() == 0
         out, steps = m.reconstruct(dev(f), dev(msk), conn=conn, op=op, return_steps=True)
         ref, n = oracle.reconstruct(f, msk, conn=conn, op=op)
         assert_same(host(out), ref, f"rec {kind} {op} conn{conn} {H}x{W}")
@@ -98,7 +118,7 @@ def test_reconstruct_parity(kind, op, conn):
     assert m.device_status() == 0
 
 
-def test_workload0_chain_and_reconstruction():
+def test_workload0_chain_and_reconstruction(kernel):
     """256x256 u8: 64-step 8-connected dilation chain, then reconstruction to stability."""
     w = synth.workload0()
     m = gm()
@@ -112,7 +132,7 @@ def test_workload0_chain_and_reconstruction():
 
 
 @pytest.mark.parametrize("kind", ["u8", "f32", "f64"])
-def test_in_place_and_strided(kind):
+def test_in_place_and_strided(kind, kernel):
     rng = np.random.default_rng(3)
     m = gm()
     f, msk = rand_pair(90, 130, kind, rng)
@@ -144,10 +164,8 @@ def test_reconstruct_not_converged_status():
     assert m.device_status() == 0  # read clears
 
 
-def test_full_size_1024_u8_chain_sampled():
-    """1024x1024 u8, 1500-step chains: the oracle is run on a 1500-step chain
-    restricted to the window that determines a sample of output rows
-    (a pixel's value after N steps depends only on pixels within N of it)."""
+def test_full_size_1024_u8_chain(kernel):
+    """1024x1024 u8 (workload 1), 100-step chains of both operations, whole image."""
     w = synth.workload1_u8()
     m = gm()
     for op, key in (("dilate", "marker_dilate"), ("erode", "marker_erode")):
