@@ -128,6 +128,45 @@ GEO_API int morph_window_erode(geo_dtype dtype, const void *in, void *out, int64
                        int64_t width, int64_t pitch, int64_t half_size, void *stream);
 
 /*
+ * Reverse mode of the masked chain (Eq. 4) for GEO_F32 / GEO_F64; the paper
+ * has no backward pass, these are this library's rules. A step computes
+ * f_t(p) = clamp(ext_{q in N(p)} f_{t-1}(q), m(p)) (ext = max and clamp =
+ * min for dilation, op = 0; the reverse for erosion, op = 1). Its upstream
+ * gradient g_t(p) goes to the mask at p when the mask is strictly beyond the
+ * neighbourhood extreme, otherwise to f_{t-1}(p + d_k) with k = (dy+1)*3 +
+ * (dx+1) the lowest neighbour index attaining the extreme. Gradients are
+ * summed as a gather over k = 0..8 in increasing order, in the element type;
+ * grad_mask accumulates over steps N, N-1, ..., 1. Results are deterministic.
+ *
+ * Images come as a batch of `batch` equal-shape images stored one after
+ * another (image b starts at ptr + b * height * pitch elements). `pitch` is
+ * shared by marker, mask, out, grad_out, grad_marker and grad_mask.
+ *
+ * geo_chain_backward_workspace_size: bytes of device workspace the pair
+ *   below needs (checkpoints every ckpt_interval steps, routing codes of one
+ *   segment, two gradient buffers); 0 for invalid arguments.
+ * geo_chain_fwd_ckpt: out = the chain of `steps` steps (as geo_dilate_chain /
+ *   geo_erode_chain), also storing the checkpoints in `workspace` (caller
+ *   owned, ws_bytes >= the size above, else GEO_ERR_WORKSPACE). out must not
+ *   alias marker.
+ * geo_chain_backward: given the same arguments and the workspace written by
+ *   geo_chain_fwd_ckpt (not modified in between), writes grad_marker =
+ *   dL/dmarker and grad_mask = dL/dmask for upstream gradient grad_out =
+ *   dL/dout. It reuses the workspace's scratch parts but leaves the
+ *   checkpoints intact, so a second backward call with the same workspace
+ *   is valid. grad buffers must not overlap each other or the inputs.
+ */
+GEO_API size_t geo_chain_backward_workspace_size(geo_dtype dtype, int64_t height, int64_t width, int64_t steps,
+                                         int ckpt_interval, int batch);
+GEO_API int geo_chain_fwd_ckpt(geo_dtype dtype, int op, const void *marker, const void *mask, void *out,
+                       int64_t height, int64_t width, int64_t pitch, int conn, int64_t steps,
+                       int ckpt_interval, int batch, void *workspace, size_t ws_bytes, void *stream);
+GEO_API int geo_chain_backward(geo_dtype dtype, int op, const void *mask, const void *grad_out,
+                       void *grad_marker, void *grad_mask, int64_t height, int64_t width,
+                       int64_t pitch, int conn, int64_t steps, int ckpt_interval, int batch,
+                       void *workspace, void *stream);
+
+/*
  * geo_dilate_chain without any memory allocation. The paper has no
  * counterpart; this exists for callers that cannot allocate GPU memory during
  * a call (a fixed memory budget owned by another allocator, a real-time loop

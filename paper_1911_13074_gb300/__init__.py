@@ -24,7 +24,8 @@ from . import build as _build
 
 __all__ = [
     "GeoError", "load", "library_path", "dilate_chain", "erode_chain", "reconstruct",
-    "window_dilate", "window_erode", "device_status", "DTYPES",
+    "window_dilate", "window_erode", "device_status", "DTYPES", "geodesic_chain",
+    "chain_fwd_ckpt", "chain_backward",
 ]
 
 GEO_U8, GEO_F32, GEO_F64 = 0, 1, 2
@@ -73,6 +74,12 @@ def load():
             fn = getattr(lib, name)
             fn.argtypes = [I, P, P, L, L, L, L, P]
             fn.restype = I
+        lib.geo_chain_backward_workspace_size.argtypes = [I, L, L, L, I, I]
+        lib.geo_chain_backward_workspace_size.restype = ctypes.c_size_t
+        lib.geo_chain_fwd_ckpt.argtypes = [I, I, P, P, P, L, L, L, I, L, I, I, P, ctypes.c_size_t, P]
+        lib.geo_chain_fwd_ckpt.restype = I
+        lib.geo_chain_backward.argtypes = [I, I, P, P, P, P, L, L, L, I, L, I, I, P, P]
+        lib.geo_chain_backward.restype = I
         _lib = lib
         return lib
 
@@ -195,3 +202,86 @@ def device_status(device=None) -> int:
         rc = lib.geo_device_status(torch.cuda.current_stream(dev).cuda_stream, ctypes.byref(v))
     _check(rc, "geo_device_status")
     return int(v.value)
+
+
+# ---------------------------------------------------------------------------
+# differentiable chain (float32 / float64)
+# ---------------------------------------------------------------------------
+
+_OPS = {"dilate": 0, "erode": 1}
+
+
+def _batch_view(t: torch.Tensor, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype not in (torch.float32, torch.float64):
+        raise TypeError(f"{name}: the backward pass supports float32 and float64, got {t.dtype}")
+    if t.dim() == 2:
+        t = t.unsqueeze(0)
+    if t.dim() != 3:
+        raise ValueError(f"{name} must be (H, W) or (B, H, W)")
+    return t.contiguous()
+
+
+def chain_fwd_ckpt(marker, mask, steps: int, conn: int = 8, op: str = "dilate", ckpt_interval: int = 32):
+    """Forward chain that also stores checkpoints; returns (out, workspace)."""
+    lib = load()
+    mk = _batch_view(marker, "marker")
+    ms = _batch_view(mask, "mask")
+    if mk.shape != ms.shape or mk.dtype != ms.dtype:
+        raise ValueError("marker and mask must match in shape and dtype")
+    B, H, W = mk.shape
+    dt = DTYPES[mk.dtype]
+    nbytes = lib.geo_chain_backward_workspace_size(dt, H, W, int(steps), int(ckpt_interval), B)
+    if nbytes == 0 and H * W > 0:
+        raise GeoError(-1, "geo_chain_backward_workspace_size")
+    ws = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=mk.device)
+    out = torch.empty_like(mk)
+    with torch.cuda.device(mk.device):
+        rc = lib.geo_chain_fwd_ckpt(dt, _OPS[op], mk.data_ptr(), ms.data_ptr(), out.data_ptr(), H, W, W, int(conn),
+                                    int(steps), int(ckpt_interval), B, ws.data_ptr(), int(nbytes), _stream(mk))
+    _check(rc, "geo_chain_fwd_ckpt")
+    return out.view(marker.shape), ws
+
+
+def chain_backward(mask, grad_out, workspace, steps: int, conn: int = 8, op: str = "dilate",
+                   ckpt_interval: int = 32):
+    """(grad_marker, grad_mask) of the chain whose forward wrote `workspace`."""
+    lib = load()
+    ms = _batch_view(mask, "mask")
+    g = _batch_view(grad_out, "grad_out").to(ms.dtype)
+    B, H, W = ms.shape
+    gmk = torch.empty_like(ms)
+    gms = torch.empty_like(ms)
+    with torch.cuda.device(ms.device):
+        rc = lib.geo_chain_backward(DTYPES[ms.dtype], _OPS[op], ms.data_ptr(), g.data_ptr(), gmk.data_ptr(),
+                                    gms.data_ptr(), H, W, W, int(conn), int(steps), int(ckpt_interval), B,
+                                    workspace.data_ptr(), _stream(ms))
+    _check(rc, "geo_chain_backward")
+    return gmk.view(mask.shape), gms.view(mask.shape)
+
+
+class _GeodesicChain(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, marker, mask, steps, conn, op, ckpt_interval):
+        out, ws = chain_fwd_ckpt(marker, mask, steps, conn, op, ckpt_interval)
+        ctx.save_for_backward(mask, ws)
+        ctx.cfg = (steps, conn, op, ckpt_interval)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        mask, ws = ctx.saved_tensors
+        steps, conn, op, ckpt = ctx.cfg
+        gmk, gms = chain_backward(mask, grad_out, ws, steps, conn, op, ckpt)
+        return gmk, gms, None, None, None, None
+
+
+def geodesic_chain(marker, mask, steps: int, conn: int = 8, op: str = "dilate", ckpt_interval: int = 32):
+    """Differentiable geodesic chain (Eq. 4) of float32/float64 (H, W) or (B, H, W) images.
+
+    The backward pass recomputes each segment of ckpt_interval steps from a
+    checkpoint and routes gradients by the lowest-index tie rule (see
+    include/geomorph.h).
+    """
+    return _GeodesicChain.apply(marker, mask, int(steps), int(conn), op, int(ckpt_interval))

@@ -70,7 +70,7 @@ static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // Choose the tile interior TH x TW and halo K. The cost model per step is
 // (waves of tiles) x (area a tile computes per step, about (TH+K)(TW+K)),
 // plus a fixed synchronisation cost per pass spread over the pass's K steps.
-int plan_tiles(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P) {
+int plan_tiles(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P, int batch) {
   const int CE = chunk_elems(dt);
   int Kmax = dt == GEO_U8 ? 24 : dt == GEO_F32 ? 12 : 6;
   if (const char *e = getenv("GEOMORPH_K")) Kmax = atoi(e);
@@ -96,7 +96,7 @@ int plan_tiles(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hin
       int bps = 0;
       if (occupancy(dt, op, conn, smem, &bps) != GEO_OK) return GEO_ERR_CUDA;
       if (bps <= 0) continue;
-      const int64_t tiles = cdiv(H, th) * cdiv(W, tw);
+      const int64_t tiles = cdiv(H, th) * cdiv(W, tw) * batch;
       const int64_t slots = (int64_t)bps * nsm;
       const int64_t grid = tiles < slots ? tiles : slots;
       // tiles share an SM when more than one CTA is resident per SM
@@ -127,7 +127,7 @@ int plan_tiles(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hin
       const size_t smem = (size_t)3 * RH * rs;
       int bps = 0;
       if (smem <= 227 * 1024 && occupancy(dt, op, conn, smem, &bps) == GEO_OK && bps > 0) {
-        const int64_t tiles = cdiv(H, th) * cdiv(W, tw);
+        const int64_t tiles = cdiv(H, th) * cdiv(W, tw) * batch;
         const int64_t slots = (int64_t)bps * nsm;
         bp = Plan{th, tw, K, rs, (int)cdiv(W, tw), (int)cdiv(H, th), (int)(tiles < slots ? tiles : slots), smem};
       }
@@ -141,12 +141,13 @@ using PlanKey = std::tuple<int, int, int, int, int64_t, int64_t, int64_t, int, s
 static std::map<PlanKey, Plan> g_plans;
 static std::mutex g_plan_mu;
 
-static int make_plan(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P) {
+static int make_plan(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P,
+                     int batch) {
   int dev = 0;
   cudaGetDevice(&dev);
   const char *ek = getenv("GEOMORPH_K");
   const char *et = getenv("GEOMORPH_TILE");
-  PlanKey key{dev, dt, op, conn, H, W, steps_hint < 64 ? steps_hint : 64, nsm, ek ? ek : "", et ? et : ""};
+  PlanKey key{dev * 1024 + batch, dt, op, conn, H, W, steps_hint < 64 ? steps_hint : 64, nsm, ek ? ek : "", et ? et : ""};
   {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     auto it = g_plans.find(key);
@@ -155,7 +156,7 @@ static int make_plan(int dt, int op, int conn, int64_t H, int64_t W, int64_t ste
       return GEO_OK;
     }
   }
-  int rc = plan_tiles(dt, op, conn, H, W, steps_hint, nsm, P);
+  int rc = plan_tiles(dt, op, conn, H, W, steps_hint, nsm, P, batch);
   if (rc == GEO_OK && getenv("GEOMORPH_DEBUG"))
     fprintf(stderr, "geomorph plan: dt=%d op=%d conn=%d %lldx%lld -> tile %dx%d K=%d tiles=%dx%d grid=%d smem=%zu\n",
             dt, op, conn, (long long)H, (long long)W, P->TH, P->TW, P->K, P->tiles_y, P->tiles_x, P->grid, P->smem);
@@ -190,7 +191,8 @@ static int occupancy_rr(int dt, int op, int conn, int *bps) {
 // one region-step (one step of one CTA on its whole region): a pass costs
 // kSyncSteps for its load / store / grid barrier, and every step costs one
 // unit per tile an SM has to process in that pass.
-static int plan_rr_uncached(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P) {
+static int plan_rr_uncached(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P,
+                            int batch) {
   const RRGeom g = rr_geom(dt);
   const int RWID = 32 * g.CW, RHGT = g.NW * g.RW * g.B;
   int bps = 0;
@@ -205,7 +207,7 @@ static int plan_rr_uncached(int dt, int op, int conn, int64_t H, int64_t W, int6
   for (int K = g.CW; K <= kmax; K += g.CW) {
     if (forceK > 0 && K != ((forceK + g.CW - 1) / g.CW) * g.CW) continue;
     const int TW = RWID - 2 * K, TH = RHGT - 2 * K;
-    const int64_t tiles = cdiv(H, TH) * cdiv(W, TW);
+    const int64_t tiles = cdiv(H, TH) * cdiv(W, TW) * batch;
     const double per_sm = (double)cdiv(tiles, nsm);
     double cost;
     if (steps_hint > 0) {
@@ -222,6 +224,7 @@ static int plan_rr_uncached(int dt, int op, int conn, int64_t H, int64_t W, int6
       best = cost;
       const int64_t slots = (int64_t)bps * nsm;
       bp = Plan{TH, TW, K, 0, (int)cdiv(W, TW), (int)cdiv(H, TH), (int)(tiles < slots ? tiles : slots), 0};
+      (void)batch;
     }
   }
   if (best >= 1e300) return GEO_ERR_ARG;
@@ -229,12 +232,13 @@ static int plan_rr_uncached(int dt, int op, int conn, int64_t H, int64_t W, int6
   return GEO_OK;
 }
 
-static int make_plan_rr(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P) {
+static int make_plan_rr(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P,
+                        int batch) {
   int dev = 0;
   cudaGetDevice(&dev);
   const char *ek = getenv("GEOMORPH_K");
   const char *es = getenv("GEOMORPH_SYNC");
-  PlanKey key{dev, dt + 16, op, conn, H, W, steps_hint, nsm, ek ? ek : "", es ? es : ""};
+  PlanKey key{dev * 1024 + batch, dt + 16, op, conn, H, W, steps_hint, nsm, ek ? ek : "", es ? es : ""};
   {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     auto it = g_plans.find(key);
@@ -243,7 +247,7 @@ static int make_plan_rr(int dt, int op, int conn, int64_t H, int64_t W, int64_t 
       return GEO_OK;
     }
   }
-  int rc = plan_rr_uncached(dt, op, conn, H, W, steps_hint, nsm, P);
+  int rc = plan_rr_uncached(dt, op, conn, H, W, steps_hint, nsm, P, batch);
   if (rc == GEO_OK && getenv("GEOMORPH_DEBUG"))
     fprintf(stderr, "geomorph rr plan: dt=%d op=%d conn=%d %lldx%lld steps=%lld -> interior %dx%d K=%d tiles=%dx%d grid=%d\n",
             dt, op, conn, (long long)H, (long long)W, (long long)steps_hint, P->TH, P->TW, P->K, P->tiles_y,
@@ -286,8 +290,9 @@ static bool overlaps(const void *a, const void *b, size_t n) {
 }
 
 // Common driver of chains, reconstruction and windows.
-static int run(int dt, const void *marker, const void *mask, void *out, int64_t H, int64_t W, int64_t pitch,
-               int conn, int op, int mode, int64_t steps, int64_t *steps_out, void *stream) {
+int run_chain(int dt, const void *marker, const void *mask, void *out, int64_t H, int64_t W, int64_t pitch, int conn,
+              int op, int mode, int64_t steps, int64_t *steps_out, void *stream, int batch) {
+  if (batch < 1) return GEO_ERR_ARG;
   if (dt != GEO_U8 && dt != GEO_F32 && dt != GEO_F64) return GEO_ERR_DTYPE;
   if (H < 0 || W < 0 || pitch < W || (conn != 4 && conn != 8) || (op != DILATE && op != ERODE))
     return GEO_ERR_ARG;
@@ -296,7 +301,7 @@ static int run(int dt, const void *marker, const void *mask, void *out, int64_t 
   const int es = elem_size(dt);
   if (!aligned(marker, es) || !aligned(out, es) || (mask && !aligned(mask, es))) return GEO_ERR_ALIGN;
   const int64_t pitch_b = pitch * es;
-  const size_t span = (size_t)((H - 1) * pitch_b + W * es);
+  const size_t span = (size_t)((int64_t)(batch - 1) * H * pitch_b + (H - 1) * pitch_b + W * es);
   if (mask && overlaps(mask, out, span)) return GEO_ERR_ARG;
   const bool alias = (marker == out);
   if (!alias && overlaps(marker, out, span)) return GEO_ERR_ARG;
@@ -304,7 +309,8 @@ static int run(int dt, const void *marker, const void *mask, void *out, int64_t 
 
   if (mode == MODE_CHAIN && steps == 0) {
     if (alias) return GEO_OK;
-    return cudaMemcpy2DAsync(out, pitch_b, marker, pitch_b, W * es, H, cudaMemcpyDeviceToDevice, s) == cudaSuccess
+    return cudaMemcpy2DAsync(out, pitch_b, marker, pitch_b, W * es, H * (int64_t)batch, cudaMemcpyDeviceToDevice,
+                             s) == cudaSuccess
                ? GEO_OK
                : GEO_ERR_CUDA;
   }
@@ -315,14 +321,14 @@ static int run(int dt, const void *marker, const void *mask, void *out, int64_t 
   const char *kern = getenv("GEOMORPH_KERNEL");
   const bool rr = !(kern && strcmp(kern, "tile") == 0);
   Plan P;
-  rc = rr ? make_plan_rr(dt, op, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P)
-          : make_plan(dt, op, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P);
+  rc = rr ? make_plan_rr(dt, op, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P, batch)
+          : make_plan(dt, op, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P, batch);
   if (rc != GEO_OK) return rc;
 
   // scratch: control words + one ping-pong image with a 16-byte aligned pitch
   const int64_t spitch_b = ((W * es + 15) / 16) * 16;
   const size_t ctl_b = 256;
-  const size_t scratch_b = ctl_b + (size_t)spitch_b * (size_t)H;
+  const size_t scratch_b = ctl_b + (size_t)spitch_b * (size_t)H * (size_t)batch;
   void *scratch = nullptr;
   if (cudaMallocFromPoolAsync(&scratch, scratch_b, ds->pool, s) != cudaSuccess) return GEO_ERR_CUDA;
   rc = GEO_OK;
@@ -334,6 +340,10 @@ static int run(int dt, const void *marker, const void *mask, void *out, int64_t 
   L.mask = make_plane(mask, pitch_b, dt, rr);
   L.out = make_plane(out, pitch_b, dt, rr);
   L.scratch = make_plane((char *)scratch + ctl_b, spitch_b, dt, rr);
+  L.marker.bstride = L.out.bstride = H * pitch_b;
+  L.mask.bstride = mask ? H * pitch_b : 0;
+  L.scratch.bstride = H * spitch_b;
+  L.batch = batch;
   L.H = H;
   L.W = W;
   L.TH = P.TH;
@@ -394,13 +404,13 @@ int geo_device_status(void *stream, int *status) {
 int geo_dilate_chain(geo_dtype dtype, const void *marker, const void *mask, void *out, int64_t height,
                      int64_t width, int64_t pitch, int conn, int64_t steps, void *stream) {
   if (steps < 0 || (!mask && height > 0 && width > 0)) return GEO_ERR_ARG;
-  return run(dtype, marker, mask, out, height, width, pitch, conn, DILATE, MODE_CHAIN, steps, nullptr, stream);
+  return run_chain(dtype, marker, mask, out, height, width, pitch, conn, DILATE, MODE_CHAIN, steps, nullptr, stream, 1);
 }
 
 int geo_erode_chain(geo_dtype dtype, const void *marker, const void *mask, void *out, int64_t height,
                     int64_t width, int64_t pitch, int conn, int64_t steps, void *stream) {
   if (steps < 0 || (!mask && height > 0 && width > 0)) return GEO_ERR_ARG;
-  return run(dtype, marker, mask, out, height, width, pitch, conn, ERODE, MODE_CHAIN, steps, nullptr, stream);
+  return run_chain(dtype, marker, mask, out, height, width, pitch, conn, ERODE, MODE_CHAIN, steps, nullptr, stream, 1);
 }
 
 int geo_reconstruct(geo_dtype dtype, const void *marker, const void *mask, void *out, int64_t height,
@@ -411,19 +421,20 @@ int geo_reconstruct(geo_dtype dtype, const void *marker, const void *mask, void 
   // default cap: every changing step of any input (at most H*W + 1) plus room
   // for the last, unchanged pass that detects the fixed point (K <= 1024)
   if (max_steps <= 0) max_steps = height * width + 1 + 1024;
-  return run(dtype, marker, mask, out, height, width, pitch, conn, op, MODE_REC, max_steps, steps_out, stream);
+  return run_chain(dtype, marker, mask, out, height, width, pitch, conn, op, MODE_REC, max_steps, steps_out, stream,
+                   1);
 }
 
 int morph_window_dilate(geo_dtype dtype, const void *in, void *out, int64_t height, int64_t width, int64_t pitch,
                         int64_t half_size, void *stream) {
   if (half_size < 0) return GEO_ERR_ARG;
-  return run(dtype, in, nullptr, out, height, width, pitch, 8, DILATE, MODE_CHAIN, half_size, nullptr, stream);
+  return run_chain(dtype, in, nullptr, out, height, width, pitch, 8, DILATE, MODE_CHAIN, half_size, nullptr, stream, 1);
 }
 
 int morph_window_erode(geo_dtype dtype, const void *in, void *out, int64_t height, int64_t width, int64_t pitch,
                        int64_t half_size, void *stream) {
   if (half_size < 0) return GEO_ERR_ARG;
-  return run(dtype, in, nullptr, out, height, width, pitch, 8, ERODE, MODE_CHAIN, half_size, nullptr, stream);
+  return run_chain(dtype, in, nullptr, out, height, width, pitch, 8, ERODE, MODE_CHAIN, half_size, nullptr, stream, 1);
 }
 
 }  // extern "C"

@@ -19,7 +19,14 @@ struct Plane {
   char *ptr;
   int64_t pitch_b;
   int vec_ok;
+  int64_t bstride;  // bytes from one image of a batch to the next
 };
+
+__host__ __device__ inline Plane plane_of(const Plane &P, int b) {
+  Plane q = P;
+  if (q.ptr) q.ptr += (int64_t)b * P.bstride;
+  return q;
+}
 
 // Inter-CTA control words, zeroed by the host before each launch.
 struct Control {
@@ -45,6 +52,7 @@ struct TileLaunch {
   Control *ctl;
   int *status;            // per-device sticky status word
   int64_t *steps_out;     // rec: optional device pointer
+  int batch;              // images of equal shape, one after another (<= 1: one image)
 };
 
 // Tile geometry of one launch: interior TH x TW, halo K, shared-memory row
@@ -55,7 +63,12 @@ struct Plan {
 };
 
 // Uncached tile planning and launch (geo_api.cu).
-int plan_tiles(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P);
+int plan_tiles(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P, int batch = 1);
+
+// Chain / reconstruction / window driver of the C ABI (geo_api.cu): a batch
+// of equal-shape images stored one after another (image stride H * pitch).
+int run_chain(int dt, const void *marker, const void *mask, void *out, int64_t H, int64_t W, int64_t pitch, int conn,
+              int op, int mode, int64_t steps, int64_t *steps_out, void *stream, int batch);
 int launch_plan(int dt, const TileLaunch &L, int op, int conn, cudaStream_t s, const Plan &P);
 
 // Host-side launcher per element type (defined in geo_tile_<dtype>.cu).

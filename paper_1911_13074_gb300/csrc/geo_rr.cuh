@@ -398,7 +398,8 @@ __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
   __shared__ int changed_s;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int K = L.K, TH = L.TH, TW = L.TW;
-  const int ntiles = L.tiles_x * L.tiles_y;
+  const int tiles_img = L.tiles_x * L.tiles_y;
+  const int ntiles = tiles_img * (L.batch > 1 ? L.batch : 1);
   const bool rec = (L.mode == MODE_REC);
   const bool virt = (L.mask.ptr == nullptr);
   const bool mask_resident = (ntiles <= (int)gridDim.x);
@@ -426,19 +427,21 @@ __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
       S = (int)(steps_left < (int64_t)K ? steps_left : (int64_t)K);
     }
     const bool to_out = rec ? (((pass + L.alias) & 1) == 0) : (((L.npasses - 1 - pass) & 1) == 0);
-    const Plane dst = to_out ? L.out : L.scratch;
-    const Plane src = (pass == 0) ? L.marker : (to_out ? L.scratch : L.out);
+    const Plane dstP = to_out ? L.out : L.scratch;
+    const Plane srcP = (pass == 0) ? L.marker : (to_out ? L.scratch : L.out);
     const bool src_cg = (pass > 0) || (L.marker.ptr == L.out.ptr);
 
     if (threadIdx.x == 0) changed_s = 0;
     bool changed = false;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      const int ty = t / L.tiles_x, tx = t - ty * L.tiles_x;
+      const int bi = t / tiles_img, tt = t - bi * tiles_img;
+      const int ty = tt / L.tiles_x, tx = tt - ty * L.tiles_x;
+      const Plane src = plane_of(srcP, bi), dst = plane_of(dstP, bi), mask = plane_of(L.mask, bi);
       const int64_t ty0 = (int64_t)ty * TH, tx0 = (int64_t)tx * TW;
       const int64_t gy0 = ty0 - K + warp * PH;
       const int64_t gx = tx0 - K + lane * CW;
       R::load_words(src, L.H, L.W, gy0, gx, src_cg, false, w);
-      if (!mask_resident || pass == 0) R::load_words(L.mask, L.H, L.W, gy0, gx, false, virt, m);
+      if (!mask_resident || pass == 0) R::load_words(mask, L.H, L.W, gy0, gx, false, virt, m);
       bool ok = true;
       for (int j = 0; j < S; ++j) {
         ok &= R::template step<CONN>(w, m, &xbuf[parity][0][0][0], &xbar, parity, lane, warp);

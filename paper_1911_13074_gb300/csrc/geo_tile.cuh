@@ -416,7 +416,8 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileLaunch L) {
   char *bufA = smem;
   char *bufB = smem + buf_b;
   char *bufM = smem + 2 * buf_b;
-  const int ntiles = L.tiles_x * L.tiles_y;
+  const int tiles_img = L.tiles_x * L.tiles_y;
+  const int ntiles = tiles_img * (L.batch > 1 ? L.batch : 1);
   const bool rec = (L.mode == MODE_REC);
   const bool virt = (L.mask.ptr == nullptr);
   // with at most one tile per CTA the mask tile stays in shared memory for
@@ -437,19 +438,21 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileLaunch L) {
       S = (int)(steps_left < (int64_t)K ? steps_left : (int64_t)K);
     }
     const bool to_out = rec ? (((pass + L.alias) & 1) == 0) : (((L.npasses - 1 - pass) & 1) == 0);
-    const Plane dst = to_out ? L.out : L.scratch;
-    const Plane src = (pass == 0) ? L.marker : (to_out ? L.scratch : L.out);
+    const Plane dstP = to_out ? L.out : L.scratch;
+    const Plane srcP = (pass == 0) ? L.marker : (to_out ? L.scratch : L.out);
     const bool src_cg = (pass > 0) || (L.marker.ptr == L.out.ptr);
 
     if (threadIdx.x == 0) changed_s = 0;
     bool changed = false;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      const int ty = t / L.tiles_x, tx = t - ty * L.tiles_x;
+      const int bi = t / tiles_img, tt = t - bi * tiles_img;
+      const int ty = tt / L.tiles_x, tx = tt - ty * L.tiles_x;
+      const Plane src = plane_of(srcP, bi), dst = plane_of(dstP, bi), mask = plane_of(L.mask, bi);
       const int64_t ty0 = (int64_t)ty * TH, tx0 = (int64_t)tx * TW;
       __syncthreads();  // previous tile's store has finished reading smem
       T::load_region(bufA, rs, src, L.H, L.W, ty0 - K, tx0 - K - CE, RH, NC, src_cg, false);
       if (!mask_resident || pass == 0)
-        T::load_region(bufM, rs, L.mask, L.H, L.W, ty0 - K, tx0 - K - CE, RH, NC, false, virt);
+        T::load_region(bufM, rs, mask, L.H, L.W, ty0 - K, tx0 - K - CE, RH, NC, false, virt);
       __syncthreads();
       char *a = bufA, *b = bufB;
       for (int j = 1; j <= S; ++j) {
