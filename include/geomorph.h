@@ -128,6 +128,52 @@ GEO_API int morph_window_erode(geo_dtype dtype, const void *in, void *out, int64
                        int64_t width, int64_t pitch, int64_t half_size, void *stream);
 
 /*
+ * Batched execution: many independent items in one persistent launch.
+ * The paper has no batched form; item i computes exactly what the matching
+ * single-item entry point computes on its own images.
+ */
+typedef struct {
+    int op;              /* 0 dilation chain, 1 erosion chain (Eq. 3-4),
+                            2 dilation by reconstruction, 3 erosion by reconstruction (Eq. 5),
+                            4 window dilation, 5 window erosion (Eq. 1-2) */
+    geo_dtype dtype;
+    int conn;            /* 4 or 8; windows are always the 8-connected square */
+    int64_t height, width, pitch;  /* pitch in elements, >= width */
+    int64_t steps;       /* chain: steps (>= 0); window: half size s (>= 0);
+                            reconstruction: max_steps (<= 0: default as geo_reconstruct) */
+    const void *marker;  /* device input (the image, for windows) */
+    const void *mask;    /* device mask (ignored for windows) */
+    void *out;           /* device output; may alias marker, must not overlap mask */
+} geo_item;
+
+/*
+ * Bytes of device workspace geo_batch needs for these items (descriptor
+ * table, per-item state, the tile work-queue, one scratch image per item);
+ * 0 if an item is invalid.
+ */
+GEO_API size_t geo_batch_workspace_size(const geo_item *items, int n);
+
+/*
+ * geo_batch = geo_batch_prepare + geo_batch_launch.
+ * geo_batch_prepare uploads the items' descriptors (tile geometry, K per
+ *   item) from host memory into the workspace; stream-ordered.
+ * geo_batch_launch resets the queue and runs every item to completion in one
+ *   persistent cooperative kernel; it copies nothing from the host, so a
+ *   prepared workspace can be launched repeatedly (and captured in a CUDA
+ *   graph) as long as the items' pointers and sizes are unchanged.
+ * status_out: optional DEVICE int[n]; item i gets GEO_OK,
+ *   GEO_ERR_NOT_CONVERGED (reconstruction cap reached) or GEO_ERR_TIMEOUT
+ *   (the launch ended before the item completed).
+ * Items are scheduled largest first; a tile of an item waits only for its
+ * own item's previous pass. Workspace contents must not be modified between
+ * prepare and launch.
+ */
+GEO_API int geo_batch_prepare(const geo_item *items, int n, void *workspace, size_t ws_bytes, void *stream);
+GEO_API int geo_batch_launch(const geo_item *items, int n, void *workspace, int *status_out, void *stream);
+GEO_API int geo_batch(const geo_item *items, int n, void *workspace, size_t ws_bytes, int *status_out,
+              void *stream);
+
+/*
  * Reverse mode of the masked chain (Eq. 4) for GEO_F32 / GEO_F64; the paper
  * has no backward pass, these are this library's rules. A step computes
  * f_t(p) = clamp(ext_{q in N(p)} f_{t-1}(q), m(p)) (ext = max and clamp =

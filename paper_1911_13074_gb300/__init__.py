@@ -25,7 +25,7 @@ from . import build as _build
 __all__ = [
     "GeoError", "load", "library_path", "dilate_chain", "erode_chain", "reconstruct",
     "window_dilate", "window_erode", "device_status", "DTYPES", "geodesic_chain",
-    "chain_fwd_ckpt", "chain_backward",
+    "chain_fwd_ckpt", "chain_backward", "Batch", "OPS",
 ]
 
 GEO_U8, GEO_F32, GEO_F64 = 0, 1, 2
@@ -45,6 +45,19 @@ class GeoError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
         super().__init__(f"{where}: {STATUS.get(code, code)}")
+
+
+class GeoItem(ctypes.Structure):
+    """Mirror of geo_item in include/geomorph.h."""
+    _fields_ = [("op", ctypes.c_int), ("dtype", ctypes.c_int), ("conn", ctypes.c_int),
+                ("height", ctypes.c_int64), ("width", ctypes.c_int64), ("pitch", ctypes.c_int64),
+                ("steps", ctypes.c_int64), ("marker", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("out", ctypes.c_void_p)]
+
+
+#: geo_item.op codes
+OPS = {"dilate_chain": 0, "erode_chain": 1, "dilate_rec": 2, "erode_rec": 3, "window_dilate": 4,
+       "window_erode": 5}
 
 
 def library_path() -> str:
@@ -80,6 +93,15 @@ def load():
         lib.geo_chain_fwd_ckpt.restype = I
         lib.geo_chain_backward.argtypes = [I, I, P, P, P, P, L, L, L, I, L, I, I, P, P]
         lib.geo_chain_backward.restype = I
+        IP = ctypes.POINTER(GeoItem)
+        lib.geo_batch_workspace_size.argtypes = [IP, I]
+        lib.geo_batch_workspace_size.restype = ctypes.c_size_t
+        lib.geo_batch_prepare.argtypes = [IP, I, P, ctypes.c_size_t, P]
+        lib.geo_batch_prepare.restype = I
+        lib.geo_batch_launch.argtypes = [IP, I, P, P, P]
+        lib.geo_batch_launch.restype = I
+        lib.geo_batch.argtypes = [IP, I, P, ctypes.c_size_t, P, P]
+        lib.geo_batch.restype = I
         _lib = lib
         return lib
 
@@ -285,3 +307,76 @@ def geodesic_chain(marker, mask, steps: int, conn: int = 8, op: str = "dilate", 
     include/geomorph.h).
     """
     return _GeodesicChain.apply(marker, mask, int(steps), int(conn), op, int(ckpt_interval))
+
+
+# ---------------------------------------------------------------------------
+# batched execution
+# ---------------------------------------------------------------------------
+
+class Batch:
+    """Many independent items run in one persistent launch (geo_batch).
+
+    items: list of dicts with keys op (a key of OPS or its code), marker,
+    mask (not for windows), steps (chain length, window half size, or
+    reconstruction max_steps with 0 = default), conn (4 or 8), and optionally
+    out (defaults to a new tensor; may be the marker for in-place).
+    prepare() uploads the descriptors; launch() runs every item (it copies
+    nothing from the host and can be captured in a CUDA graph).
+    """
+
+    def __init__(self, items):
+        lib = load()
+        self.n = len(items)
+        arr = (GeoItem * max(self.n, 1))()
+        self.outs = []
+        self._keep = []
+        dev = None
+        for i, it in enumerate(items):
+            op = OPS[it["op"]] if isinstance(it["op"], str) else int(it["op"])
+            mk = _image(it["marker"], "marker")
+            dev = mk.device
+            win = op in (4, 5)
+            ms = None if win else _image(it["mask"], "mask")
+            if ms is not None:
+                _same(mk, ms, "mask")
+            out = it.get("out")
+            out = _out_like(mk, out)
+            H, W = mk.shape
+            arr[i].op = op
+            arr[i].dtype = DTYPES[mk.dtype]
+            arr[i].conn = int(it.get("conn", 8))
+            arr[i].height, arr[i].width, arr[i].pitch = H, W, _pitch(mk)
+            arr[i].steps = int(it.get("steps", 0))
+            arr[i].marker = mk.data_ptr()
+            arr[i].mask = None if ms is None else ms.data_ptr()
+            arr[i].out = out.data_ptr()
+            self.outs.append(out)
+            self._keep += [mk, ms]
+        self.items = arr
+        self.device = dev if dev is not None else torch.device("cuda", torch.cuda.current_device())
+        nbytes = lib.geo_batch_workspace_size(arr, self.n)
+        if nbytes == 0 and self.n > 0:
+            raise GeoError(-1, "geo_batch_workspace_size")
+        self.workspace = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=self.device)
+        self.nbytes = int(nbytes)
+        self.status = torch.zeros(max(self.n, 1), dtype=torch.int32, device=self.device)
+
+    def prepare(self):
+        lib = load()
+        with torch.cuda.device(self.device):
+            rc = lib.geo_batch_prepare(self.items, self.n, self.workspace.data_ptr(), self.nbytes,
+                                       torch.cuda.current_stream(self.device).cuda_stream)
+        _check(rc, "geo_batch_prepare")
+        return self
+
+    def launch(self):
+        lib = load()
+        with torch.cuda.device(self.device):
+            rc = lib.geo_batch_launch(self.items, self.n, self.workspace.data_ptr(), self.status.data_ptr(),
+                                      torch.cuda.current_stream(self.device).cuda_stream)
+        _check(rc, "geo_batch_launch")
+        return self.outs
+
+    def run(self):
+        self.prepare()
+        return self.launch()

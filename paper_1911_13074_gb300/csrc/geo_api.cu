@@ -52,6 +52,14 @@ static int device_state(DeviceState **out) {
   return GEO_OK;
 }
 
+int device_status_word(int **status) {
+  DeviceState *ds = nullptr;
+  const int rc = device_state(&ds);
+  if (rc != GEO_OK) return rc;
+  *status = ds->status;
+  return GEO_OK;
+}
+
 // ---------------------------------------------------------------------------
 // planning
 // ---------------------------------------------------------------------------

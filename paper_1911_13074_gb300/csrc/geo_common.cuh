@@ -62,6 +62,9 @@ struct Plan {
   size_t smem;
 };
 
+// The per-device status word that device-side waits report into (geo_api.cu).
+int device_status_word(int **status);
+
 // Uncached tile planning and launch (geo_api.cu).
 int plan_tiles(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P, int batch = 1);
 
