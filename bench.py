@@ -41,6 +41,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="geomorph", choices=["geomorph", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-secondary", action="store_true",
+                   help="skip the batched and forward+backward comparisons")
     return p.parse_args()
 
 
@@ -176,6 +178,84 @@ def cpu_baseline():
             "sample": f"1024x1024 u8 8-connected dilation chain, {n} of the 1500 steps, {dt:.1f} s"}
 
 
+def _time(fn, reps, warmup=1):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def secondary(dev):
+    """The batched and forward+backward forms against the plain path, same GPU."""
+    import torch
+    import paper_1911_13074_gb300 as gm
+    import synth
+    res = {}
+    # batched: workload 3 (512 items) in one launch vs 512 single-item calls
+    w3 = synth.workload3()
+    items = []
+    for it in w3:
+        items.append({"op": it["op"], "marker": torch.from_numpy(it["marker"]).to(dev),
+                      "mask": torch.from_numpy(it["mask"]).to(dev),
+                      "steps": 0 if it["steps"] < 0 else it["steps"], "conn": it["conn"]})
+    batch = gm.Batch(items).prepare()
+    t_batch = _time(batch.launch, 3)
+    ok = bool((batch.status[:len(items)] == 0).all().item())
+
+    def plain():
+        for it, out in zip(items, batch.outs):
+            op = it["op"]
+            if op in (0, 1):
+                (gm.dilate_chain if op == 0 else gm.erode_chain)(it["marker"], it["mask"], it["steps"],
+                                                                conn=it["conn"], out=out)
+            else:
+                gm.reconstruct(it["marker"], it["mask"], conn=it["conn"], op="dilate" if op == 2 else "erode",
+                               out=out)
+    t_plain = _time(plain, 3)
+    chain_px_steps = sum(int(it["marker"].numel()) * it["steps"] for it in items if it["op"] in (0, 1))
+    res["batched"] = {
+        "workload": "512 items, H,W log-uniform [64,2048] (W not a multiple of 32), half u8 half f32, "
+                    "steps U{8..1500}, 25% to stability, op and conn drawn per item (synthetic workload 3)",
+        "ms_batched": t_batch * 1e3, "ms_plain_512_calls": t_plain * 1e3, "speed_ratio_vs_plain": t_plain / t_batch,
+        "chain_items_gpixel_steps_per_s": chain_px_steps / t_batch / 1e9, "all_items_ok": ok,
+        "gpu_launches_batched": 2, "gpu_launches_plain": len(items)}
+    del items, batch, w3
+    torch.cuda.empty_cache()
+    # forward + backward: workload 4 (32 x 512^2 f32, 256 steps) vs the plain forward
+    w4 = synth.workload4()
+    mk, ms, g = (torch.from_numpy(w4[k]).to(dev) for k in ("marker", "mask", "grad_out"))
+    steps = 256
+    fb = {}
+    for C in (16, 32, 64):
+        def fwd_bwd(C=C):
+            out, ws = gm.chain_fwd_ckpt(mk, ms, steps, conn=8, ckpt_interval=C)
+            gm.chain_backward(ms, g, ws, steps, conn=8, ckpt_interval=C)
+        fb[C] = _time(fwd_bwd, 3)
+    out1 = torch.empty_like(mk)
+
+    def plain_fwd():
+        for b in range(mk.shape[0]):
+            gm.dilate_chain(mk[b], ms[b], steps, conn=8, out=out1[b])
+    t_pf = _time(plain_fwd, 3)
+    px = mk.numel() * steps
+    res["fwd_bwd"] = {
+        "workload": "32 x 512x512 float32, 8-connected 256-step dilation chain (synthetic workload 4)",
+        "ms_plain_forward_32_calls": t_pf * 1e3,
+        "plain_forward_gpixel_steps_per_s": px / t_pf / 1e9,
+        "ms_fwd_bwd": {str(C): t * 1e3 for C, t in fb.items()},
+        "speed_ratio_vs_plain_forward": {str(C): t_pf / t for C, t in fb.items()},
+    }
+    return res
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup(args.gpus)
@@ -281,6 +361,8 @@ def main():
                      "peak_basis": f"{nsm} SMs x 128 lanes/clk x 2 px (max.u16x2) x {sm_max:.0f} MHz",
                      "ops_per_pixel_step": OPS_PER_PX_STEP},
     }
+    if not args.no_secondary and world == 1:
+        line.update(secondary(dev))
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

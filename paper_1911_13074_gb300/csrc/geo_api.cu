@@ -211,7 +211,9 @@ static int plan_rr_uncached(int dt, int op, int conn, int64_t H, int64_t W, int6
   if (const char *e = getenv("GEOMORPH_K")) forceK = atoi(e);
   double best = 1e300;
   Plan bp{};
-  const int kmax = (RWID < RHGT ? RWID : RHGT) / 2 - g.CW;
+  // K <= min(TH, TW): a tile's halo then reaches only its 8 neighbours,
+  // which is what the point-to-point pass synchronisation assumes
+  const int kmax = (RWID < RHGT ? RWID : RHGT) / 3;
   for (int K = g.CW; K <= kmax; K += g.CW) {
     if (forceK > 0 && K != ((forceK + g.CW - 1) / g.CW) * g.CW) continue;
     const int TW = RWID - 2 * K, TH = RHGT - 2 * K;
@@ -333,9 +335,11 @@ int run_chain(int dt, const void *marker, const void *mask, void *out, int64_t H
           : make_plan(dt, op, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P, batch);
   if (rc != GEO_OK) return rc;
 
-  // scratch: control words + one ping-pong image with a 16-byte aligned pitch
+  // scratch: control words (+ per-tile pass epochs of the register kernel)
+  // and one ping-pong image with a 16-byte aligned pitch
   const int64_t spitch_b = ((W * es + 15) / 16) * 16;
-  const size_t ctl_b = 256;
+  const size_t ntiles = (size_t)P.tiles_x * (size_t)P.tiles_y * (size_t)batch;
+  const size_t ctl_b = 256 + ((ntiles * sizeof(int) + 255) / 256) * 256;
   const size_t scratch_b = ctl_b + (size_t)spitch_b * (size_t)H * (size_t)batch;
   void *scratch = nullptr;
   if (cudaMallocFromPoolAsync(&scratch, scratch_b, ds->pool, s) != cudaSuccess) return GEO_ERR_CUDA;
@@ -364,6 +368,7 @@ int run_chain(int dt, const void *marker, const void *mask, void *out, int64_t H
   L.steps = steps;
   L.alias = alias ? 1 : 0;
   L.ctl = (Control *)scratch;
+  L.epoch = (int *)((char *)scratch + 256);
   L.status = ds->status;
   L.steps_out = steps_out;
   if (mode == MODE_CHAIN) {

@@ -83,7 +83,7 @@ __device__ __forceinline__ int pass_steps(const BItem &it, int p, int64_t steps_
 
 // One tile of one pass with element policy P: load, S steps, store.
 template <class P, int CONN>
-__device__ bool run_tile(const BItem &it, int tile, int p, int S, typename P::Wd *xb, uint64_t *bar,
+__device__ bool run_tile(const BItem &it, int tile, int p, int S, typename P::Wd *xb, uint64_t *bars,
                          int &parity) {
   using R = RR<P>;
   using Wd = typename P::Wd;
@@ -102,7 +102,7 @@ __device__ bool run_tile(const BItem &it, int tile, int p, int S, typename P::Wd
   R::load_words(it.mask, it.H, it.W, gy0, gx, false, it.mask.ptr == nullptr, m);
   bool ok = true;
   for (int j = 0; j < S; ++j) {
-    ok &= R::template step<CONN>(w, m, xb + (size_t)parity * (kBatchNW + 2) * 2 * R::RWID, bar, parity, lane, warp);
+    ok &= R::template step<CONN>(w, m, xb + (size_t)parity * (kBatchNW + 2) * 2 * R::RWID, bars, parity, lane, warp);
     parity ^= 1;
   }
   const bool changed = R::store(w, dst, src, it.rec != 0, it.H, it.W, ty0, tx0, it.K, it.TH, it.TW, lane, warp);
@@ -110,21 +110,21 @@ __device__ bool run_tile(const BItem &it, int tile, int p, int S, typename P::Wd
 }
 
 template <class P>
-__device__ bool dispatch_conn(const BItem &it, int tile, int p, int S, char *xb, uint64_t *bar, int &parity) {
+__device__ bool dispatch_conn(const BItem &it, int tile, int p, int S, char *xb, uint64_t *bars, int &parity) {
   using Wd = typename P::Wd;
-  if (it.conn == 8) return run_tile<P, 8>(it, tile, p, S, reinterpret_cast<Wd *>(xb), bar, parity);
-  return run_tile<P, 4>(it, tile, p, S, reinterpret_cast<Wd *>(xb), bar, parity);
+  if (it.conn == 8) return run_tile<P, 8>(it, tile, p, S, reinterpret_cast<Wd *>(xb), bars, parity);
+  return run_tile<P, 4>(it, tile, p, S, reinterpret_cast<Wd *>(xb), bars, parity);
 }
 
-__device__ bool dispatch(const BItem &it, int tile, int p, int S, char *xb, uint64_t *bar, int &parity) {
+__device__ bool dispatch(const BItem &it, int tile, int p, int S, char *xb, uint64_t *bars, int &parity) {
   if (it.dtype == GEO_U8)
-    return it.op == DILATE ? dispatch_conn<RU8<DILATE>>(it, tile, p, S, xb, bar, parity)
-                           : dispatch_conn<RU8<ERODE>>(it, tile, p, S, xb, bar, parity);
+    return it.op == DILATE ? dispatch_conn<RU8<DILATE>>(it, tile, p, S, xb, bars, parity)
+                           : dispatch_conn<RU8<ERODE>>(it, tile, p, S, xb, bars, parity);
   if (it.dtype == GEO_F32)
-    return it.op == DILATE ? dispatch_conn<RF32<DILATE>>(it, tile, p, S, xb, bar, parity)
-                           : dispatch_conn<RF32<ERODE>>(it, tile, p, S, xb, bar, parity);
-  return it.op == DILATE ? dispatch_conn<RF64<DILATE>>(it, tile, p, S, xb, bar, parity)
-                         : dispatch_conn<RF64<ERODE>>(it, tile, p, S, xb, bar, parity);
+    return it.op == DILATE ? dispatch_conn<RF32<DILATE>>(it, tile, p, S, xb, bars, parity)
+                           : dispatch_conn<RF32<ERODE>>(it, tile, p, S, xb, bars, parity);
+  return it.op == DILATE ? dispatch_conn<RF64<DILATE>>(it, tile, p, S, xb, bars, parity)
+                         : dispatch_conn<RF64<ERODE>>(it, tile, p, S, xb, bars, parity);
 }
 
 // identity words for the slots above warp 0 / below the last warp
@@ -190,14 +190,14 @@ __global__ void batch_init(BatchArgs A, const int *order, unsigned long long nta
 
 __global__ void __launch_bounds__(kBatchNW * 32, 1) batch_kernel(BatchArgs A) {
   __shared__ __align__(16) char xb[2 * (kBatchNW + 2) * 2 * 128 * 4];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t xbar;  // split-phase step barrier of the whole CTA
   __shared__ unsigned long long task_s;
   __shared__ int flag_s, push_s, next_s, pass_s;
   __shared__ int64_t sdone_s;
   __shared__ BItem it_s;
-  if (threadIdx.x == 0) mbar_init(&bar, blockDim.x);
+  if (threadIdx.x == 0) mbar_init(&xbar, kBatchNW * 32);
   __syncthreads();
-  int parity = 0;  // phase parity of `bar`, one phase per step
+  int parity = 0;  // parity of the steps done by this CTA: exchange buffer and barrier phase
   const unsigned long long NONE = ~0ull;
   for (;;) {
     if (threadIdx.x == 0) {
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kBatchNW * 32, 1) batch_kernel(BatchArgs A) {
     __syncthreads();
     if (threadIdx.x == 0) flag_s = 0;
     __syncthreads();
-    const bool ch = dispatch(it, tile, p, S, xb, &bar, parity);
+    const bool ch = dispatch(it, tile, p, S, xb, &xbar, parity);
     if (ch) flag_s = 1;
     __syncthreads();
     // completion of this tile; the last tile of the pass schedules the next

@@ -53,6 +53,7 @@ struct TileLaunch {
   int *status;            // per-device sticky status word
   int64_t *steps_out;     // rec: optional device pointer
   int batch;              // images of equal shape, one after another (<= 1: one image)
+  int *epoch;             // register kernel, chains: per tile, passes completed
 };
 
 // Tile geometry of one launch: interior TH x TW, halo K, shared-memory row

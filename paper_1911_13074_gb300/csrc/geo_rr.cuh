@@ -169,11 +169,11 @@ struct RF64 {
   }
 };
 
-// ---------------------------------------------------------------------------
-// split-phase CTA barrier on an mbarrier in shared memory
-// ---------------------------------------------------------------------------
-
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// ---------------------------------------------------------------------------
+// mbarrier helpers (shared memory, CTA scope)
+// ---------------------------------------------------------------------------
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -269,43 +269,69 @@ struct RR {
     h[CW - 1] = P::ext3(row[CW - 2], row[CW - 1], right);
   }
 
-  // One elementary step, in place, on the lane's words. The band's top and
-  // bottom rows are published to the neighbouring warps through xb; the
-  // split-phase barrier `bar` lets the warp update its inner rows (which need
-  // no neighbour data) before it waits for the other warps' rows. Returns
-  // false if that wait expired.
+  // One elementary step, in place, on the lane's words. The band's boundary
+  // rows go to the neighbouring warps through xb (double-buffered by step
+  // parity). The CTA-wide mbarrier `bar` is split-phase: every thread
+  // arrives once its rows are written, updates its inner rows (which need no
+  // neighbour data), and only then waits for the phase. A phase completes
+  // only when every warp has arrived for that step, and a warp arrives for
+  // the next step only after its wait, so the parity of the step identifies
+  // the phase and the double buffer is never overwritten before it was read. For 8-connectivity the
+  // exchanged rows are the row 3-extremes h (what the neighbour needs), for
+  // 4-connectivity the pixels themselves. Returns false if the wait expired.
   template <int CONN>
   __device__ static bool step(Wd (&w)[RW][CW], const Wd (&m)[RW][CW], Wd *xb, uint64_t *bar, uint32_t parity,
                               int lane, int warp) {
     static_assert(RW >= 2, "a band needs distinct first and last word rows");
     Wd *mine = xb + (size_t)(warp + 1) * 2 * RWID + lane * CW;
-    *reinterpret_cast<uint4 *>(mine) = P::pack(w[0]);
-    *reinterpret_cast<uint4 *>(mine + RWID) = P::pack(w[RW - 1]);
-    mbar_arrive(bar);
-    // row 3-extremes of every old row; old boundary rows; the parts of the
-    // boundary rows' results that need no neighbour-warp data
-    Wd h[RW][CW], first[CW], last[CW], pre0[CW], preL[CW];
+    const Wd *up_slot = xb + (size_t)warp * 2 * RWID + RWID + lane * CW;
+    const Wd *dn_slot = xb + (size_t)(warp + 2) * 2 * RWID + lane * CW;
+    Wd h[RW][CW];
+    if constexpr (CONN == 8) {
+      hrow(w[0], h[0]);
+      hrow(w[RW - 1], h[RW - 1]);
+      *reinterpret_cast<uint4 *>(mine) = P::pack(h[0]);
+      *reinterpret_cast<uint4 *>(mine + RWID) = P::pack(h[RW - 1]);
+      mbar_arrive(bar);
 #pragma unroll
-    for (int r = 0; r < RW; ++r) hrow(w[r], h[r]);
+      for (int r = 1; r < RW - 1; ++r) hrow(w[r], h[r]);
+      Wd pre0[CW], preL[CW];
 #pragma unroll
-    for (int c = 0; c < CW; ++c) {
-      first[c] = w[0][c];
-      last[c] = w[RW - 1][c];
-      if constexpr (CONN == 8) {
+      for (int c = 0; c < CW; ++c) {
         pre0[c] = P::e2(h[0][c], h[1][c]);
         preL[c] = P::e2(h[RW - 2][c], h[RW - 1][c]);
-      } else {
-        pre0[c] = P::e2(h[0][c], w[1][c]);
-        preL[c] = P::e2(w[RW - 2][c], h[RW - 1][c]);
       }
-    }
-    // inner rows 1 .. RW-2
-    if constexpr (CONN == 8) {
 #pragma unroll
       for (int r = 1; r < RW - 1; ++r)
 #pragma unroll
         for (int c = 0; c < CW; ++c) w[r][c] = P::clamp(P::ext3(h[r - 1][c], h[r][c], h[r + 1][c]), m[r][c]);
+      const bool ok = mbar_wait(bar, parity);
+      Wd ha[CW], hb[CW];
+      P::unpack(*reinterpret_cast<const uint4 *>(up_slot), ha);
+      P::unpack(*reinterpret_cast<const uint4 *>(dn_slot), hb);
+#pragma unroll
+      for (int c = 0; c < CW; ++c) {
+        // row 3-extremes of the rows just above / below the band halves
+        const Wd hu = P::up(ha[c], h[RW - 1][c]);
+        const Wd hd = P::down(h[0][c], hb[c]);
+        w[0][c] = P::clamp(P::e2(pre0[c], hu), m[0][c]);
+        w[RW - 1][c] = P::clamp(P::e2(preL[c], hd), m[RW - 1][c]);
+      }
+      return ok;
     } else {
+      *reinterpret_cast<uint4 *>(mine) = P::pack(w[0]);
+      *reinterpret_cast<uint4 *>(mine + RWID) = P::pack(w[RW - 1]);
+      mbar_arrive(bar);
+      Wd first[CW], last[CW], pre0[CW], preL[CW];
+#pragma unroll
+      for (int r = 0; r < RW; ++r) hrow(w[r], h[r]);
+#pragma unroll
+      for (int c = 0; c < CW; ++c) {
+        first[c] = w[0][c];
+        last[c] = w[RW - 1][c];
+        pre0[c] = P::e2(h[0][c], w[1][c]);
+        preL[c] = P::e2(w[RW - 2][c], h[RW - 1][c]);
+      }
       Wd fp[CW];
 #pragma unroll
       for (int c = 0; c < CW; ++c) fp[c] = first[c];
@@ -318,33 +344,17 @@ struct RR {
           fp[c] = old;
         }
       }
-    }
-    const bool ok = mbar_wait(bar, parity);
-    Wd above[CW], below[CW], upw[CW], dnw[CW];
-    P::unpack(*reinterpret_cast<const uint4 *>(xb + (size_t)warp * 2 * RWID + RWID + lane * CW), above);
-    P::unpack(*reinterpret_cast<const uint4 *>(xb + (size_t)(warp + 2) * 2 * RWID + lane * CW), below);
-#pragma unroll
-    for (int c = 0; c < CW; ++c) {
-      upw[c] = P::up(above[c], last[c]);
-      dnw[c] = P::down(first[c], below[c]);
-    }
-    if constexpr (CONN == 8) {
-      Wd hu[CW], hd[CW];
-      hrow(upw, hu);
-      hrow(dnw, hd);
+      const bool ok = mbar_wait(bar, parity);
+      Wd above[CW], below[CW];
+      P::unpack(*reinterpret_cast<const uint4 *>(up_slot), above);
+      P::unpack(*reinterpret_cast<const uint4 *>(dn_slot), below);
 #pragma unroll
       for (int c = 0; c < CW; ++c) {
-        w[0][c] = P::clamp(P::e2(pre0[c], hu[c]), m[0][c]);
-        w[RW - 1][c] = P::clamp(P::e2(preL[c], hd[c]), m[RW - 1][c]);
+        w[0][c] = P::clamp(P::e2(pre0[c], P::up(above[c], last[c])), m[0][c]);
+        w[RW - 1][c] = P::clamp(P::e2(preL[c], P::down(first[c], below[c])), m[RW - 1][c]);
       }
-    } else {
-#pragma unroll
-      for (int c = 0; c < CW; ++c) {
-        w[0][c] = P::clamp(P::e2(pre0[c], upw[c]), m[0][c]);
-        w[RW - 1][c] = P::clamp(P::e2(preL[c], dnw[c]), m[RW - 1][c]);
-      }
+      return ok;
     }
-    return ok;
   }
 
   // store the interior part of the lane's words to D; with cmp, report
@@ -389,6 +399,28 @@ struct RR {
   }
 };
 
+// Wait until every tile of the 3x3 tile neighbourhood of (ty, tx) has
+// published epoch >= want. Bounded; false if the wait expired.
+__device__ __forceinline__ bool wait_neighbours(const int *epoch, int ty, int tx, int tiles_y, int tiles_x,
+                                                int want) {
+  const unsigned long long t0 = globaltimer_ns();
+  for (int dy = -1; dy <= 1; ++dy) {
+    const int ny = ty + dy;
+    if (ny < 0 || ny >= tiles_y) continue;
+    for (int dx = -1; dx <= 1; ++dx) {
+      const int nx = tx + dx;
+      if (nx < 0 || nx >= tiles_x || (dx == 0 && dy == 0)) continue;
+      const unsigned *f = reinterpret_cast<const unsigned *>(epoch) + ny * tiles_x + nx;
+      unsigned spins = 0;
+      while ((int)ld_acquire_u32(f) < want) {
+        if ((++spins & 255u) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) return false;
+      }
+    }
+  }
+  __threadfence();
+  return true;
+}
+
 template <class P, int CONN>
 __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
   using R = RR<P>;
@@ -404,7 +436,7 @@ __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
   const bool virt = (L.mask.ptr == nullptr);
   const bool mask_resident = (ntiles <= (int)gridDim.x);
 
-  __shared__ __align__(8) uint64_t xbar;
+  __shared__ __align__(8) uint64_t xbar;  // split-phase step barrier of the whole CTA
   if (threadIdx.x == 0) mbar_init(&xbar, NW * 32);
   // the slots above warp 0 and below warp NW-1 hold the identity
   for (int i = threadIdx.x; i < 2 * 2 * RWID; i += NW * 32) {
@@ -416,7 +448,7 @@ __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
 
   Wd w[RW][CW], m[RW][CW];
   int64_t steps_left = L.steps, steps_done = 0;
-  int parity = 0;
+  int parity = 0;  // parity of the steps done by this CTA: exchange buffer and barrier phase
   for (int pass = 0;; ++pass) {
     int S;
     if (!rec) {
@@ -440,6 +472,14 @@ __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
       const int64_t ty0 = (int64_t)ty * TH, tx0 = (int64_t)tx * TW;
       const int64_t gy0 = ty0 - K + warp * PH;
       const int64_t gx = tx0 - K + lane * CW;
+      if (!rec && pass > 0) {
+        // chains synchronise point to point: the tiles whose interiors this
+        // tile's halo reads must have finished the previous pass (which also
+        // means they are done reading the buffer this pass overwrites)
+        if (threadIdx.x == 0 && !wait_neighbours(L.epoch + (size_t)bi * tiles_img, ty, tx, L.tiles_y, L.tiles_x, pass))
+          record_status(L.status, GEO_ERR_TIMEOUT);
+        __syncthreads();
+      }
       R::load_words(src, L.H, L.W, gy0, gx, src_cg, false, w);
       if (!mask_resident || pass == 0) R::load_words(mask, L.H, L.W, gy0, gx, false, virt, m);
       bool ok = true;
@@ -449,6 +489,13 @@ __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
       }
       if (!ok) record_status(L.status, GEO_ERR_TIMEOUT);
       changed |= R::store(w, dst, src, rec, L.H, L.W, ty0, tx0, K, TH, TW, lane, warp);
+      if (!rec && pass + 1 < L.npasses) {
+        __syncthreads();  // every thread's stores of this tile are issued
+        if (threadIdx.x == 0) {
+          __threadfence();
+          st_release_u32(reinterpret_cast<unsigned *>(L.epoch) + t, (unsigned)(pass + 1));
+        }
+      }
     }
     if (rec) {
       if (changed) changed_s = 1;
@@ -459,8 +506,10 @@ __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
       }
       steps_done += S;
       steps_left -= S;
-    } else if (pass == L.npasses - 1) {
-      break;
+    } else {
+      if (pass == L.npasses - 1) break;
+      if (*(volatile int *)L.status != 0) return;
+      continue;  // no grid barrier between chain passes
     }
     if (!grid_barrier(L.ctl, L.status, gridDim.x)) return;
     if (rec) {
