@@ -174,6 +174,30 @@ GEO_API int geo_batch(const geo_item *items, int n, void *workspace, size_t ws_b
               void *stream);
 
 /*
+ * Autotuning of the pass length K (which fixes the tile interior), persisted.
+ * The paper has no counterpart (its CPU pipeline has no tile size).
+ * geo_autotune times every valid K for each item (a geo_item as above; the
+ *   call runs the item's operation on its own buffers several times, so out
+ *   is overwritten), keeps the fastest per (dtype, op, conn, height, width,
+ *   chain-length class) in the library's tune table and, if cache_path is
+ *   not NULL, writes the whole table there. Synchronous. GEOMORPH_K must not
+ *   be set (GEO_ERR_ARG).
+ * geo_tune_load reads such a file into the tune table (entries from any
+ *   device). The environment variable GEOMORPH_TUNE_CACHE names a file that
+ *   is loaded on first use, keeping only entries tuned on the same device
+ *   model.
+ * geo_tune_lookup returns the tuned K for that key, or 0. Chain lengths of 64
+ *   and more share one class; reconstruction ignores steps.
+ * geo_plan_info reports the K and tile interior (TH x TW) the single-image
+ *   entry points use for these arguments (op as in geo_item).
+ */
+GEO_API int geo_autotune(const geo_item *items, int n, const char *cache_path);
+GEO_API int geo_tune_load(const char *cache_path);
+GEO_API int geo_tune_lookup(int dtype, int op, int conn, int64_t height, int64_t width, int64_t steps);
+GEO_API int geo_plan_info(geo_dtype dtype, int op, int conn, int64_t height, int64_t width, int64_t steps,
+                  int *K, int *TH, int *TW);
+
+/*
  * Reverse mode of the masked chain (Eq. 4) for GEO_F32 / GEO_F64; the paper
  * has no backward pass, these are this library's rules. A step computes
  * f_t(p) = clamp(ext_{q in N(p)} f_{t-1}(q), m(p)) (ext = max and clamp =

@@ -25,7 +25,7 @@ from . import build as _build
 __all__ = [
     "GeoError", "load", "library_path", "dilate_chain", "erode_chain", "reconstruct",
     "window_dilate", "window_erode", "device_status", "DTYPES", "geodesic_chain",
-    "chain_fwd_ckpt", "chain_backward", "Batch", "OPS",
+    "chain_fwd_ckpt", "chain_backward", "Batch", "OPS", "autotune", "tune_load", "tune_lookup", "plan_info",
 ]
 
 GEO_U8, GEO_F32, GEO_F64 = 0, 1, 2
@@ -70,7 +70,9 @@ def load():
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.build()
+        # GEOMORPH_LIB selects another build of the same sources (a variant
+        # compiled with other band shapes); otherwise build in-tree
+        path = os.environ.get("GEOMORPH_LIB") or _build.build()
         lib = ctypes.CDLL(path)
         P, I, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
         lib.geo_status_string.argtypes = [I]
@@ -102,6 +104,15 @@ def load():
         lib.geo_batch_launch.restype = I
         lib.geo_batch.argtypes = [IP, I, P, ctypes.c_size_t, P, P]
         lib.geo_batch.restype = I
+        lib.geo_autotune.argtypes = [IP, I, ctypes.c_char_p]
+        lib.geo_autotune.restype = I
+        lib.geo_tune_load.argtypes = [ctypes.c_char_p]
+        lib.geo_tune_load.restype = I
+        lib.geo_tune_lookup.argtypes = [I, I, I, L, L, L]
+        lib.geo_tune_lookup.restype = I
+        IPtr = ctypes.POINTER(I)
+        lib.geo_plan_info.argtypes = [I, I, I, L, L, L, IPtr, IPtr, IPtr]
+        lib.geo_plan_info.restype = I
         _lib = lib
         return lib
 
@@ -380,3 +391,38 @@ class Batch:
     def run(self):
         self.prepare()
         return self.launch()
+
+
+# ---------------------------------------------------------------------------
+# autotuning
+# ---------------------------------------------------------------------------
+
+def autotune(items, cache_path=None):
+    """Time every valid pass length K for each item (dicts as for Batch) and
+    keep the fastest in the library's tune table; write it to cache_path."""
+    b = Batch(items)  # builds the geo_item array and output buffers
+    lib = load()
+    with torch.cuda.device(b.device):
+        rc = lib.geo_autotune(b.items, b.n, None if cache_path is None else str(cache_path).encode())
+    _check(rc, "geo_autotune")
+    return b.outs
+
+
+def tune_load(cache_path):
+    _check(load().geo_tune_load(str(cache_path).encode()), "geo_tune_load")
+
+
+def tune_lookup(dtype, op, conn, height, width, steps) -> int:
+    dt = DTYPES[dtype] if isinstance(dtype, torch.dtype) else int(dtype)
+    code = OPS[op] if isinstance(op, str) else int(op)
+    return int(load().geo_tune_lookup(dt, code, int(conn), int(height), int(width), int(steps)))
+
+
+def plan_info(dtype, op, conn, height, width, steps):
+    """(K, TH, TW) that the single-image entry points use for these arguments."""
+    dt = DTYPES[dtype] if isinstance(dtype, torch.dtype) else int(dtype)
+    code = OPS[op] if isinstance(op, str) else int(op)
+    K, TH, TW = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().geo_plan_info(dt, code, int(conn), int(height), int(width), int(steps), ctypes.byref(K),
+                                ctypes.byref(TH), ctypes.byref(TW)), "geo_plan_info")
+    return K.value, TH.value, TW.value

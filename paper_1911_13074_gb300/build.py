@@ -47,18 +47,25 @@ def _digest(paths, extra=""):
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, defines=(), out_dir: str = OUT) -> str:
+    """Compile csrc/*.cu in parallel and link libgeomorph.so into out_dir.
+
+    defines: extra preprocessor definitions ("NAME=VALUE"), e.g. to build a
+    variant with other register-kernel band shapes into another directory.
+    """
     srcs, deps = _sources()
-    os.makedirs(OUT, exist_ok=True)
-    stamp = os.path.join(OUT, "stamp")
-    dig = _digest(srcs + deps, " ".join(ARCH + FLAGS))
-    if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dig:
-        return LIB
+    os.makedirs(out_dir, exist_ok=True)
+    lib_path = os.path.join(out_dir, "libgeomorph.so")
+    stamp = os.path.join(out_dir, "stamp")
+    dflags = [f"-D{d}" for d in defines]
+    dig = _digest(srcs + deps, " ".join(ARCH + FLAGS + dflags))
+    if not force and os.path.exists(lib_path) and os.path.exists(stamp) and open(stamp).read() == dig:
+        return lib_path
     nv = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(OUT, os.path.basename(src) + ".o")
-        cmd = [nv, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
+        cmd = [nv, *ARCH, *FLAGS, *dflags, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -72,14 +79,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for _, log in results:
             sys.stderr.write(log)
     objs = [o for o, _ in results]
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     r = subprocess.run([nv, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib_path)
     with open(stamp, "w") as fh:
         fh.write(dig)
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -182,11 +182,11 @@ static int make_plan(int dt, int op, int conn, int64_t H, int64_t W, int64_t ste
 struct RRGeom {
   int CW, RW, NW, B;
 };
-// must match RU8 / RF32 / RF64 in geo_rr.cuh
+// must match SU8 / SF32 / SF64 in geo_rr.cuh (CW, RW, NW, bands)
 static RRGeom rr_geom(int dt) {
-  if (dt == GEO_U8) return RRGeom{4, 8, 8, 2};
-  if (dt == GEO_F32) return RRGeom{4, 16, 8, 1};
-  return RRGeom{2, 16, 8, 1};
+  if (dt == GEO_U8) return RRGeom{4, GEO_RR_U8_RW, GEO_RR_U8_NW, 2};
+  if (dt == GEO_F32) return RRGeom{4, GEO_RR_F32_RW, GEO_RR_F32_NW, 1};
+  return RRGeom{2, GEO_RR_F64_RW, GEO_RR_F64_NW, 1};
 }
 
 static int occupancy_rr(int dt, int op, int conn, int *bps) {
@@ -200,14 +200,16 @@ static int occupancy_rr(int dt, int op, int conn, int *bps) {
 // kSyncSteps for its load / store / grid barrier, and every step costs one
 // unit per tile an SM has to process in that pass.
 static int plan_rr_uncached(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P,
-                            int batch) {
+                            int batch, int tunedK) {
   const RRGeom g = rr_geom(dt);
   const int RWID = 32 * g.CW, RHGT = g.NW * g.RW * g.B;
   int bps = 0;
   if (occupancy_rr(dt, op, conn, &bps) != GEO_OK || bps <= 0) return GEO_ERR_CUDA;
   double kSyncSteps = 10.0;
   if (const char *e = getenv("GEOMORPH_SYNC")) kSyncSteps = atof(e);
-  int forceK = 0;
+  // K fixed by the GEOMORPH_K override, else by the tune cache, else chosen
+  // by the cost model below
+  int forceK = tunedK;
   if (const char *e = getenv("GEOMORPH_K")) forceK = atoi(e);
   double best = 1e300;
   Plan bp{};
@@ -242,29 +244,34 @@ static int plan_rr_uncached(int dt, int op, int conn, int64_t H, int64_t W, int6
   return GEO_OK;
 }
 
-static int make_plan_rr(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P,
-                        int batch) {
+using RRPlanKey = std::tuple<int, int, int, int, int, int64_t, int64_t, int64_t, int, std::string, std::string, int>;
+static std::map<RRPlanKey, Plan> g_rr_plans;
+
+// code: the operation as a geo_item.op code (0..5), for the tune cache
+static int make_plan_rr(int dt, int op, int code, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm,
+                        Plan *P, int batch) {
   int dev = 0;
   cudaGetDevice(&dev);
   const char *ek = getenv("GEOMORPH_K");
   const char *es = getenv("GEOMORPH_SYNC");
-  PlanKey key{dev * 1024 + batch, dt + 16, op, conn, H, W, steps_hint, nsm, ek ? ek : "", es ? es : ""};
+  const int tk = ek ? 0 : tuned_k(dt, code, conn, H, W, steps_hint);
+  RRPlanKey key{dev, batch, dt, op, conn, H, W, steps_hint, nsm, ek ? ek : "", es ? es : "", tk};
   {
     std::lock_guard<std::mutex> lk(g_plan_mu);
-    auto it = g_plans.find(key);
-    if (it != g_plans.end()) {
+    auto it = g_rr_plans.find(key);
+    if (it != g_rr_plans.end()) {
       *P = it->second;
       return GEO_OK;
     }
   }
-  int rc = plan_rr_uncached(dt, op, conn, H, W, steps_hint, nsm, P, batch);
+  int rc = plan_rr_uncached(dt, op, conn, H, W, steps_hint, nsm, P, batch, tk);
   if (rc == GEO_OK && getenv("GEOMORPH_DEBUG"))
     fprintf(stderr, "geomorph rr plan: dt=%d op=%d conn=%d %lldx%lld steps=%lld -> interior %dx%d K=%d tiles=%dx%d grid=%d\n",
             dt, op, conn, (long long)H, (long long)W, (long long)steps_hint, P->TH, P->TW, P->K, P->tiles_y,
             P->tiles_x, P->grid);
   if (rc == GEO_OK) {
     std::lock_guard<std::mutex> lk(g_plan_mu);
-    g_plans[key] = *P;
+    g_rr_plans[key] = *P;
   }
   return rc;
 }
@@ -331,7 +338,8 @@ int run_chain(int dt, const void *marker, const void *mask, void *out, int64_t H
   const char *kern = getenv("GEOMORPH_KERNEL");
   const bool rr = !(kern && strcmp(kern, "tile") == 0);
   Plan P;
-  rc = rr ? make_plan_rr(dt, op, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P, batch)
+  const int code = mode == MODE_REC ? 2 + op : (mask ? op : 4 + op);
+  rc = rr ? make_plan_rr(dt, op, code, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P, batch)
           : make_plan(dt, op, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P, batch);
   if (rc != GEO_OK) return rc;
 
@@ -399,6 +407,24 @@ const char *geo_status_string(int status) {
     case GEO_ERR_WORKSPACE: return "GEO_ERR_WORKSPACE: workspace too small";
     default: return "unknown geo_status";
   }
+}
+
+int geo_plan_info(geo_dtype dtype, int op, int conn, int64_t height, int64_t width, int64_t steps, int *K, int *TH,
+                  int *TW) {
+  if (dtype != GEO_U8 && dtype != GEO_F32 && dtype != GEO_F64) return GEO_ERR_DTYPE;
+  if (op < 0 || op > 5 || height <= 0 || width <= 0 || (op < 4 && conn != 4 && conn != 8)) return GEO_ERR_ARG;
+  DeviceState *ds = nullptr;
+  int rc = device_state(&ds);
+  if (rc != GEO_OK) return rc;
+  const bool rec = (op == 2 || op == 3);
+  const int eop = (op == 1 || op == 3 || op == 5) ? ERODE : DILATE;
+  Plan P;
+  rc = make_plan_rr(dtype, eop, op, op >= 4 ? 8 : conn, height, width, rec ? 0 : steps, ds->nsm, &P, 1);
+  if (rc != GEO_OK) return rc;
+  if (K) *K = P.K;
+  if (TH) *TH = P.TH;
+  if (TW) *TW = P.TW;
+  return GEO_OK;
 }
 
 int geo_device_status(void *stream, int *status) {

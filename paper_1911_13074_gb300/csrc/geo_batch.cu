@@ -334,6 +334,11 @@ int item_k(const geo_item &x) {
     int k = ((atoi(e) + g.CW - 1) / g.CW) * g.CW;
     if (k >= g.CW && k <= kmax) return k;
   }
+  {
+    // a measured K for this item shape (geo_autotune) takes precedence
+    const int tk = tuned_k(x.dtype, x.op, is_win(x) ? 8 : x.conn, x.height, x.width, x.steps);
+    if (tk >= g.CW && tk <= kmax && tk % g.CW == 0) return tk;
+  }
   const bool rec = is_rec(x);
   const double sync = 10.0;
   double best = 1e300;

@@ -13,6 +13,21 @@ enum Mode : int { MODE_CHAIN = 0, MODE_REC = 1 };
 
 constexpr int kThreads = 256;  // threads per CTA of the tile kernels
 
+// Band height (word rows per warp) and warps per CTA of the single-image
+// register-resident kernel, per element type.
+#ifndef GEO_RR_U8_RW
+#define GEO_RR_U8_RW 4
+#define GEO_RR_U8_NW 16
+#endif
+#ifndef GEO_RR_F32_RW
+#define GEO_RR_F32_RW 8
+#define GEO_RR_F32_NW 16
+#endif
+#ifndef GEO_RR_F64_RW
+#define GEO_RR_F64_RW 8
+#define GEO_RR_F64_NW 16
+#endif
+
 // One image operand of a pass: base pointer, row stride in bytes, and
 // whether 16-byte vector access is legal (base and stride 16-byte aligned).
 struct Plane {
@@ -62,6 +77,10 @@ struct Plan {
   int TH, TW, K, rs, tiles_x, tiles_y, grid;
   size_t smem;
 };
+
+// Tuned pass length K for an item-op code (0..5 as geo_item.op), or 0 when
+// the tune cache has no entry (geo_tune.cu).
+int tuned_k(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps);
 
 // The per-device status word that device-side waits report into (geo_api.cu).
 int device_status_word(int **status);

@@ -35,6 +35,7 @@ static int occupancy_impl(int op, int conn, size_t smem, int *bps) {
 
 template <template <int> class RP>
 static void *rr_kernel_ptr(int op, int conn) {
+  // RP is one of the single-image policies SU8 / SF32 / SF64
   if (op == DILATE) return conn == 8 ? (void *)rr_kernel<RP<DILATE>, 8> : (void *)rr_kernel<RP<DILATE>, 4>;
   return conn == 8 ? (void *)rr_kernel<RP<ERODE>, 8> : (void *)rr_kernel<RP<ERODE>, 4>;
 }

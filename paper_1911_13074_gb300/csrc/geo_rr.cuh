@@ -36,12 +36,12 @@ namespace geo {
 // register-resident element policies
 // ---------------------------------------------------------------------------
 
-template <int OP>
+template <int OP, int RW_ = 4, int NW_ = 16>
 struct RU8 {
   using Wd = uint32_t;  // two u16 lanes: rows r and r + RW of one column
   using Px = uint32_t;  // one pixel value (0..255)
   using G = uint8_t;
-  static constexpr int BANDS = 2, CW = 4, RW = 4, NW = 16, GS = 1;
+  static constexpr int BANDS = 2, CW = 4, RW = RW_, NW = NW_, GS = 1;
   __device__ static Wd e2(Wd a, Wd b) { return OP == DILATE ? umax2(a, b) : umin2(a, b); }
   __device__ static Wd ext3(Wd a, Wd b, Wd c) { return e2(e2(a, b), c); }
   __device__ static Wd clamp(Wd v, Wd m) { return OP == DILATE ? umin2(v, m) : umax2(v, m); }
@@ -83,12 +83,12 @@ struct RU8 {
   }
 };
 
-template <int OP>
+template <int OP, int RW_ = 8, int NW_ = 16>
 struct RF32 {
   using Wd = float;
   using Px = float;
   using G = float;
-  static constexpr int BANDS = 1, CW = 4, RW = 8, NW = 16, GS = 4;
+  static constexpr int BANDS = 1, CW = 4, RW = RW_, NW = NW_, GS = 4;
   __device__ static Wd e2(Wd a, Wd b) { return OP == DILATE ? fmaxf(a, b) : fminf(a, b); }
   __device__ static Wd ext3(Wd a, Wd b, Wd c) { return OP == DILATE ? fmax3(a, b, c) : fmin3(a, b, c); }
   __device__ static Wd clamp(Wd v, Wd m) { return OP == DILATE ? fminf(v, m) : fmaxf(v, m); }
@@ -127,12 +127,12 @@ struct RF32 {
   }
 };
 
-template <int OP>
+template <int OP, int RW_ = 8, int NW_ = 16>
 struct RF64 {
   using Wd = long long;  // order-preserving key of the double
   using Px = long long;
   using G = double;
-  static constexpr int BANDS = 1, CW = 2, RW = 8, NW = 16, GS = 8;
+  static constexpr int BANDS = 1, CW = 2, RW = RW_, NW = NW_, GS = 8;
   __device__ static Wd e2(Wd a, Wd b) { return OP == DILATE ? max(a, b) : min(a, b); }
   __device__ static Wd ext3(Wd a, Wd b, Wd c) { return e2(e2(a, b), c); }
   __device__ static Wd clamp(Wd v, Wd m) { return OP == DILATE ? min(v, m) : max(v, m); }
@@ -202,6 +202,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     if ((++n & 1023u) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) return false;
   }
 }
+
+// Policies of the single-image kernel (the batch kernel uses the defaults).
+// Taller bands put more work between a warp's arrival and its wait at the
+// step barrier; the host planner (rr_geom in geo_api.cu) mirrors these.
+template <int OP> using SU8 = RU8<OP, GEO_RR_U8_RW, GEO_RR_U8_NW>;
+template <int OP> using SF32 = RF32<OP, GEO_RR_F32_RW, GEO_RR_F32_NW>;
+template <int OP> using SF64 = RF64<OP, GEO_RR_F64_RW, GEO_RR_F64_NW>;
 
 // ---------------------------------------------------------------------------
 // the kernel

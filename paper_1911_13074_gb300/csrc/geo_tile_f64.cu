@@ -1,4 +1,5 @@
-// Tile-kernel instantiations for f64 images.
+// Kernel instantiations for f64 images: the shared-memory tile kernel and the
+// register-resident kernel.
 #include "geo_launch.cuh"
 
 namespace geo {
@@ -10,9 +11,9 @@ int launch_tile_f64(const TileLaunch &L, int op, int conn, cudaStream_t s, int g
 int occupancy_tile_f64(int op, int conn, size_t smem, int *bps) { return occupancy_impl<EF64>(op, conn, smem, bps); }
 
 int launch_rr_f64(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid) {
-  return launch_rr_impl<RF64>(L, op, conn, s, grid);
+  return launch_rr_impl<SF64>(L, op, conn, s, grid);
 }
 
-int occupancy_rr_f64(int op, int conn, int *bps) { return occupancy_rr_impl<RF64>(op, conn, bps); }
+int occupancy_rr_f64(int op, int conn, int *bps) { return occupancy_rr_impl<SF64>(op, conn, bps); }
 
 }  // namespace geo

@@ -1,4 +1,5 @@
-// Tile-kernel instantiations for u8 images.
+// Kernel instantiations for u8 images: the shared-memory tile kernel and the
+// register-resident kernel.
 #include "geo_launch.cuh"
 
 namespace geo {
@@ -10,9 +11,9 @@ int launch_tile_u8(const TileLaunch &L, int op, int conn, cudaStream_t s, int gr
 int occupancy_tile_u8(int op, int conn, size_t smem, int *bps) { return occupancy_impl<EU8>(op, conn, smem, bps); }
 
 int launch_rr_u8(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid) {
-  return launch_rr_impl<RU8>(L, op, conn, s, grid);
+  return launch_rr_impl<SU8>(L, op, conn, s, grid);
 }
 
-int occupancy_rr_u8(int op, int conn, int *bps) { return occupancy_rr_impl<RU8>(op, conn, bps); }
+int occupancy_rr_u8(int op, int conn, int *bps) { return occupancy_rr_impl<SU8>(op, conn, bps); }
 
 }  // namespace geo

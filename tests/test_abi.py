@@ -60,3 +60,23 @@ def test_host_argument_checks_need_no_device():
     # misaligned float pointer, mask overlapping out
     assert lib.geo_dilate_chain(1, 18, 64, 128, 2, 2, 2, 8, 1, None) == -3
     assert lib.geo_dilate_chain(0, 0x1000, 0x2000, 0x2000, 2, 2, 2, 8, 1, None) == -1
+
+
+def test_tune_cache_file_round_trip(tmp_path):
+    """The tune-cache text format loads into the table (no device needed)."""
+    import paper_1911_13074_gb300 as gm
+    path = tmp_path / "tune.txt"
+    path.write_text("geomorph-tune 1 Some_GPU\n"
+                    "0 0 8 1024 1024 64 20 1.08\n"
+                    "1 2 4 300 200 -1 12 0.50\n"
+                    "not an entry\n")
+    gm.tune_load(path)
+    assert gm.tune_lookup(0, 0, 8, 1024, 1024, 1500) == 20   # long chains share the class 64
+    assert gm.tune_lookup(0, 0, 8, 1024, 1024, 40) == 0      # a short chain is its own class
+    assert gm.tune_lookup(1, "dilate_rec", 4, 300, 200, 0) == 12
+    assert gm.tune_lookup(2, 0, 8, 1024, 1024, 1500) == 0
+    bad = tmp_path / "bad.txt"
+    bad.write_text("something else\n")
+    import pytest as _pt
+    with _pt.raises(gm.GeoError):
+        gm.tune_load(bad)
