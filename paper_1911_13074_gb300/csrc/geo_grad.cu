@@ -29,80 +29,80 @@ namespace geo {
 namespace {
 
 constexpr uint8_t kRouteMask = 9;
-constexpr int kGradThreads = 256;
 
 template <int CONN>
 __device__ __forceinline__ bool in_shape(int k) {
   return CONN == 8 || k == 1 || k == 3 || k == 4 || k == 5 || k == 7;
 }
 
-// One recomputed forward step with routing codes. f and fo are packed
+// Launch shape of the per-step kernels: one thread per pixel, a 32 x 8
+// block of a row band, blockIdx.z = image of the batch.
+constexpr int kBX = 32, kBY = 8;
+
+// One recomputed forward step with routing codes. f, fo and code are packed
 // (row stride W); the mask has the caller's row stride.
 template <typename T, int OP, int CONN>
-__global__ void __launch_bounds__(kGradThreads) route_step(const T *__restrict__ f, const T *__restrict__ mask,
-                                                           T *__restrict__ fo, uint8_t *__restrict__ code, int64_t H,
-                                                           int64_t W, int64_t mpitch, int batch) {
-  const int64_t n = (int64_t)batch * H * W;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = i / (H * W), r = i - b * H * W;
-    const int64_t y = r / W, x = r - y * W;
-    const T *fb = f + b * H * W;
-    T best = T(0);
-    int bk = -1;
+__global__ void __launch_bounds__(kBX * kBY) route_step(const T *__restrict__ f, const T *__restrict__ mask,
+                                                        T *__restrict__ fo, uint8_t *__restrict__ code, int H, int W,
+                                                        int64_t mpitch) {
+  const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
+  if (x >= W || y >= H) return;
+  const size_t img = (size_t)blockIdx.z * H * W;
+  const T *fb = f + img;
+  T best = T(0);
+  int bk = -1;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      if (!in_shape<CONN>(k)) continue;
-      const int64_t qy = y + k / 3 - 1, qx = x + k % 3 - 1;
-      if (qy < 0 || qy >= H || qx < 0 || qx >= W) continue;
-      const T v = fb[qy * W + qx];
-      if (bk < 0 || (OP == DILATE ? (v > best) : (v < best))) {
-        best = v;
-        bk = k;
-      }
+  for (int k = 0; k < 9; ++k) {
+    if (!in_shape<CONN>(k)) continue;
+    const int qy = y + k / 3 - 1, qx = x + k % 3 - 1;
+    if (qy < 0 || qy >= H || qx < 0 || qx >= W) continue;  // clipped neighbourhood
+    const T v = fb[qy * W + qx];
+    if (bk < 0 || (OP == DILATE ? (v > best) : (v < best))) {
+      best = v;
+      bk = k;
     }
-    const T mv = mask[b * H * mpitch + y * mpitch + x];
-    const bool to_mask = (OP == DILATE) ? (mv < best) : (mv > best);
-    fo[i] = to_mask ? mv : best;
-    code[i] = to_mask ? kRouteMask : (uint8_t)bk;
   }
+  const T mv = mask[(size_t)blockIdx.z * H * mpitch + (size_t)y * mpitch + x];
+  const bool to_mask = (OP == DILATE) ? (mv < best) : (mv > best);
+  const size_t i = img + (size_t)y * W + x;
+  fo[i] = to_mask ? mv : best;
+  code[i] = to_mask ? kRouteMask : (uint8_t)bk;
 }
 
 // One reverse step: g_out = gather of g_in along the routing codes; the mask
-// gradient accumulates g_in where the code selects the mask. Row strides:
-// g_in gi_pitch, g_out go_pitch, grad_mask gm_pitch (elements).
+// gradient accumulates g_in where the code selects the mask (zero_mask: this
+// is the first reverse step, so it is written instead). Row strides: g_in
+// gi_pitch, g_out go_pitch, grad_mask gm_pitch (elements); codes packed.
 template <typename T, int CONN>
-__global__ void __launch_bounds__(kGradThreads) gather_step(const T *__restrict__ g_in, int64_t gi_pitch,
-                                                            const uint8_t *__restrict__ code, T *__restrict__ g_out,
-                                                            int64_t go_pitch, T *__restrict__ gmask, int64_t gm_pitch,
-                                                            int64_t H, int64_t W, int batch) {
-  const int64_t n = (int64_t)batch * H * W;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = i / (H * W), r = i - b * H * W;
-    const int64_t y = r / W, x = r - y * W;
-    const uint8_t *cb = code + b * H * W;
-    const T *gb = g_in + b * H * gi_pitch;
-    T acc = T(0);
+__global__ void __launch_bounds__(kBX * kBY) gather_step(const T *__restrict__ g_in, int64_t gi_pitch,
+                                                         const uint8_t *__restrict__ code, T *__restrict__ g_out,
+                                                         int64_t go_pitch, T *__restrict__ gmask, int64_t gm_pitch,
+                                                         int H, int W, int zero_mask) {
+  const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
+  if (x >= W || y >= H) return;
+  const uint8_t *cb = code + (size_t)blockIdx.z * H * W;
+  const T *gb = g_in + (size_t)blockIdx.z * H * gi_pitch;
+  T acc = T(0);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      if (!in_shape<CONN>(k)) continue;
-      const int64_t py = y - (k / 3 - 1), px = x - (k % 3 - 1);
-      if (py < 0 || py >= H || px < 0 || px >= W) continue;
-      if (cb[py * W + px] == k) acc += gb[py * gi_pitch + px];
-    }
-    if (cb[r] == kRouteMask) gmask[b * H * gm_pitch + y * gm_pitch + x] += gb[y * gi_pitch + x];
-    g_out[b * H * go_pitch + y * go_pitch + x] = acc;
+  for (int k = 0; k < 9; ++k) {
+    if (!in_shape<CONN>(k)) continue;
+    // the pixel p = q - d_k, if routed to its neighbour k, lands on q
+    const int py = y - (k / 3 - 1), px = x - (k % 3 - 1);
+    if (py < 0 || py >= H || px < 0 || px >= W) continue;
+    if (cb[py * W + px] == k) acc += gb[(size_t)py * gi_pitch + px];
   }
+  T *gm = gmask + (size_t)blockIdx.z * H * gm_pitch + (size_t)y * gm_pitch + x;
+  const bool to_mask = cb[y * W + x] == kRouteMask;
+  if (zero_mask) *gm = to_mask ? gb[(size_t)y * gi_pitch + x] : T(0);
+  else if (to_mask) *gm += gb[(size_t)y * gi_pitch + x];
+  g_out[(size_t)blockIdx.z * H * go_pitch + (size_t)y * go_pitch + x] = acc;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kGradThreads) zero_plane(T *__restrict__ p, int64_t pitch, int64_t H, int64_t W,
-                                                           int batch) {
-  const int64_t n = (int64_t)batch * H * W;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = i / (H * W), r = i - b * H * W;
-    const int64_t y = r / W, x = r - y * W;
-    p[b * H * pitch + y * pitch + x] = T(0);
-  }
+__global__ void __launch_bounds__(kBX * kBY) zero_plane(T *__restrict__ p, int64_t pitch, int H, int W) {
+  const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
+  if (x >= W || y >= H) return;
+  p[(size_t)blockIdx.z * H * pitch + (size_t)y * pitch + x] = T(0);
 }
 
 struct Layout {
@@ -129,22 +129,21 @@ Layout layout(int es, int64_t H, int64_t W, int64_t steps, int C, int batch) {
   return L;
 }
 
-int grid_for(int64_t n) {
-  int64_t g = (n + kGradThreads - 1) / kGradThreads;
-  if (g > 152 * 16) g = 152 * 16;
-  return (int)(g < 1 ? 1 : g);
+dim3 step_grid(int64_t H, int64_t W, int batch) {
+  return dim3((unsigned)((W + kBX - 1) / kBX), (unsigned)((H + kBY - 1) / kBY), (unsigned)batch);
 }
 
 template <typename T>
-int backward_impl(int op, int conn, const T *mask, const T *grad_out, T *grad_marker, T *grad_mask, int64_t H,
-                  int64_t W, int64_t pitch, int64_t steps, int C, int batch, const char *ws, cudaStream_t s) {
-  const Layout Lw = layout((int)sizeof(T), H, W, steps, C, batch);
+int backward_impl(int op, int conn, const T *mask, const T *grad_out, T *grad_marker, T *grad_mask, int64_t H64,
+                  int64_t W64, int64_t pitch, int64_t steps, int C, int batch, const char *ws, cudaStream_t s) {
+  const Layout Lw = layout((int)sizeof(T), H64, W64, steps, C, batch);
   const int64_t n = Lw.npx;
-  const int g = grid_for(n);
-  zero_plane<T><<<g, kGradThreads, 0, s>>>(grad_mask, pitch, H, W, batch);
+  const int H = (int)H64, W = (int)W64;
+  const dim3 grid = step_grid(H64, W64, batch), block(kBX, kBY);
   if (steps == 0) {
-    if (cudaMemcpy2DAsync(grad_marker, pitch * sizeof(T), grad_out, pitch * sizeof(T), W * sizeof(T),
-                          H * (int64_t)batch, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    zero_plane<T><<<grid, block, 0, s>>>(grad_mask, pitch, H, W);
+    if (cudaMemcpy2DAsync(grad_marker, pitch * sizeof(T), grad_out, pitch * sizeof(T), W64 * sizeof(T),
+                          H64 * (int64_t)batch, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
       return GEO_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? GEO_OK : GEO_ERR_CUDA;
   }
@@ -165,11 +164,11 @@ int backward_impl(int op, int conn, const T *mask, const T *grad_out, T *grad_ma
       T *fnext = st[(t - t0 - 1) & 1];
       uint8_t *ct = code + (size_t)(t - t0 - 1) * (size_t)n;
       if (op == DILATE) {
-        if (conn == 8) route_step<T, DILATE, 8><<<g, kGradThreads, 0, s>>>(fcur, mask, fnext, ct, H, W, pitch, batch);
-        else route_step<T, DILATE, 4><<<g, kGradThreads, 0, s>>>(fcur, mask, fnext, ct, H, W, pitch, batch);
+        if (conn == 8) route_step<T, DILATE, 8><<<grid, block, 0, s>>>(fcur, mask, fnext, ct, H, W, pitch);
+        else route_step<T, DILATE, 4><<<grid, block, 0, s>>>(fcur, mask, fnext, ct, H, W, pitch);
       } else {
-        if (conn == 8) route_step<T, ERODE, 8><<<g, kGradThreads, 0, s>>>(fcur, mask, fnext, ct, H, W, pitch, batch);
-        else route_step<T, ERODE, 4><<<g, kGradThreads, 0, s>>>(fcur, mask, fnext, ct, H, W, pitch, batch);
+        if (conn == 8) route_step<T, ERODE, 8><<<grid, block, 0, s>>>(fcur, mask, fnext, ct, H, W, pitch);
+        else route_step<T, ERODE, 4><<<grid, block, 0, s>>>(fcur, mask, fnext, ct, H, W, pitch);
       }
       fcur = fnext;
     }
@@ -186,12 +185,13 @@ int backward_impl(int op, int conn, const T *mask, const T *grad_out, T *grad_ma
         gnext_pitch = W;
         gsel ^= 1;
       }
+      const int first = (t == steps);
       if (conn == 8)
-        gather_step<T, 8><<<g, kGradThreads, 0, s>>>(gcur, gcur_pitch, ct, gnext, gnext_pitch, grad_mask, pitch, H, W,
-                                                     batch);
+        gather_step<T, 8><<<grid, block, 0, s>>>(gcur, gcur_pitch, ct, gnext, gnext_pitch, grad_mask, pitch, H, W,
+                                                 first);
       else
-        gather_step<T, 4><<<g, kGradThreads, 0, s>>>(gcur, gcur_pitch, ct, gnext, gnext_pitch, grad_mask, pitch, H, W,
-                                                     batch);
+        gather_step<T, 4><<<grid, block, 0, s>>>(gcur, gcur_pitch, ct, gnext, gnext_pitch, grad_mask, pitch, H, W,
+                                                 first);
       gcur = gnext;
       gcur_pitch = gnext_pitch;
     }
@@ -254,6 +254,11 @@ int geo_chain_fwd_ckpt(geo_dtype dtype, int op, const void *marker, const void *
   return GEO_OK;
 }
 
+// the per-step kernels index with 32-bit pixel coordinates on a 3-D grid
+static bool grad_shape_ok(int64_t height, int64_t width, int batch) {
+  return height <= (int64_t)65535 * 8 && width <= (int64_t)1 << 30 && batch <= 65535;
+}
+
 int geo_chain_backward(geo_dtype dtype, int op, const void *mask, const void *grad_out, void *grad_marker,
                        void *grad_mask, int64_t height, int64_t width, int64_t pitch, int conn, int64_t steps,
                        int ckpt_interval, int batch, void *workspace, void *stream) {
@@ -262,7 +267,8 @@ int geo_chain_backward(geo_dtype dtype, int op, const void *mask, const void *gr
       height < 0 || width < 0 || pitch < width)
     return GEO_ERR_ARG;
   if (height == 0 || width == 0) return GEO_OK;
-  if (!mask || !grad_out || !grad_marker || !grad_mask || !workspace) return GEO_ERR_ARG;
+  if (!mask || !grad_out || !grad_marker || !grad_mask || !workspace || !grad_shape_ok(height, width, batch))
+    return GEO_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (dtype == GEO_F32)
     return backward_impl<float>(op, conn, (const float *)mask, (const float *)grad_out, (float *)grad_marker,
