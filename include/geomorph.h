@@ -213,8 +213,9 @@ GEO_API int geo_plan_info(geo_dtype dtype, int op, int conn, int64_t height, int
  * shared by marker, mask, out, grad_out, grad_marker and grad_mask.
  *
  * geo_chain_backward_workspace_size: bytes of device workspace the pair
- *   below needs (checkpoints every ckpt_interval steps, routing codes of one
- *   segment, two gradient buffers); 0 for invalid arguments.
+ *   below needs (checkpoints every ckpt_interval steps, 1 <= ckpt_interval
+ *   <= 512, the recomputed states of one segment at every 8th step, two
+ *   gradient buffers); 0 for invalid arguments.
  * geo_chain_fwd_ckpt: out = the chain of `steps` steps (as geo_dilate_chain /
  *   geo_erode_chain), also storing the checkpoints in `workspace` (caller
  *   owned, ws_bytes >= the size above, else GEO_ERR_WORKSPACE). out must not
