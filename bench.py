@@ -253,6 +253,30 @@ def secondary(dev):
         "ms_fwd_bwd": {str(C): t * 1e3 for C, t in fb.items()},
         "speed_ratio_vs_plain_forward": {str(C): t_pf / t for C, t in fb.items()},
     }
+    del mk, ms, g, w4
+    torch.cuda.empty_cache()
+    # reconstruction to stability: workload 2 (4096^2 blob masks), both markers
+    w2 = synth.workload2()
+    rec = {}
+    for kind in ("u8", "f32"):
+        mask = torch.from_numpy(w2["mask_u8" if kind == "u8" else "mask_f32"]).to(dev)
+        markers = {"opening_31x31": gm.window_erode(mask, 15),
+                   "hdome_minus20": torch.from_numpy(w2["hdome_marker_" + kind]).to(dev)}
+        for name, marker in markers.items():
+            out = torch.empty_like(marker)
+            steps_box = {}
+
+            def run():
+                _, st = gm.reconstruct(marker, mask, conn=8, out=out, return_steps=True)
+                steps_box["s"] = st
+            t = _time(run, 3)
+            n = int(steps_box["s"].item())
+            rec[f"{kind}_{name}"] = {"ms": t * 1e3, "steps_applied": n,
+                                     "gpixel_steps_per_s": mask.numel() * n / t / 1e9}
+    res["reconstruct_4096"] = {
+        "workload": "4096x4096 blob masks (synthetic workload 2), 8-connected dilation by reconstruction to "
+                    "stability; steps_applied counts whole passes up to the first unchanged pass",
+        **rec}
     return res
 
 

@@ -66,6 +66,16 @@ def _load():
             lib.oracle_window.restype = I
             lib.oracle_chain_backward.argtypes = [P, P, P, P, P, L, L, I, I, L]
             lib.oracle_chain_backward.restype = I
+            D = ctypes.c_double
+            for name in ("oracle_hmax", "oracle_dome"):
+                getattr(lib, name).argtypes = [P, P, L, L, I, D, D, I]
+                getattr(lib, name).restype = L
+            lib.oracle_hfill.argtypes = [P, P, L, L, I]
+            lib.oracle_hfill.restype = L
+            lib.oracle_raobj.argtypes = [P, P, L, L, I, I]
+            lib.oracle_raobj.restype = L
+            lib.oracle_open_rec.argtypes = [P, P, L, L, I, L]
+            lib.oracle_open_rec.restype = L
             _lib = lib
     return _lib
 
@@ -78,7 +88,8 @@ def use_library(path):
     prev = _load()
     lib = ctypes.CDLL(path)
     for name in ("oracle_step", "oracle_chain", "oracle_reconstruct", "oracle_window",
-                 "oracle_chain_backward"):
+                 "oracle_chain_backward", "oracle_hmax", "oracle_dome", "oracle_hfill", "oracle_raobj",
+                 "oracle_open_rec"):
         fn, ref = getattr(lib, name), getattr(prev, name)
         fn.argtypes, fn.restype = ref.argtypes, ref.restype
     with _lock:
@@ -173,3 +184,57 @@ def chain_backward(f, m, grad_out, steps, conn=8, op="dilate"):
     if rc != 0:
         raise MemoryError("oracle_chain_backward failed")
     return gmk, gms
+
+
+# ---------------------------------------------------------------------------
+# geodesic operators (Section 2, Eq. 6-12)
+# ---------------------------------------------------------------------------
+
+def _op_call(name, f, *args):
+    lib = _load()
+    f64 = _f64(f)
+    out = np.empty_like(f64)
+    H, W = f64.shape
+    r = getattr(lib, name)(_ptr(f64), _ptr(out), H, W, *args)
+    if r == -2:
+        raise MemoryError(name)
+    return _back(out, np.asarray(f))
+
+
+def _lo(f):
+    return 0.0 if np.asarray(f).dtype == np.uint8 else -np.inf
+
+
+def _f32(f):
+    return 1 if np.asarray(f).dtype == np.float32 else 0
+
+
+def _h(f, h):
+    # uint8 images take an integral h (rounded down); float images take h as
+    # given, rounded to float32 for float32 images inside the oracle
+    return float(np.floor(h)) if np.asarray(f).dtype == np.uint8 else float(h)
+
+
+def hmax(f, h, conn=8):
+    """HMAX_h(f) = delta_rec^f(f - h) (Eq. 6); the u8 marker saturates at 0."""
+    return _op_call("oracle_hmax", f, conn, _h(f, h), _lo(f), _f32(f))
+
+
+def dome(f, h, conn=8):
+    """DOME_h(f) = f - HMAX_h(f) (Eq. 7)."""
+    return _op_call("oracle_dome", f, conn, _h(f, h), _lo(f), _f32(f))
+
+
+def hfill(f, conn=8):
+    """HFILL(f) = eps_rec^f(m_HFILL(f)) (Eq. 8-9)."""
+    return _op_call("oracle_hfill", f, conn)
+
+
+def raobj(f, conn=8):
+    """RAOBJ(f) = f - delta_rec^f(m_RAOBJ(f)) (Eq. 10-11)."""
+    return _op_call("oracle_raobj", f, conn, _f32(f))
+
+
+def open_rec(f, s, conn=8):
+    """gamma_rec^s(f) = delta_rec^f(eps_s(f)) (Eq. 12)."""
+    return _op_call("oracle_open_rec", f, conn, int(s))

@@ -225,3 +225,103 @@ int oracle_chain_backward(const double *f0, const double *m, const double *gout,
     free(states); free(gnew); free(sel);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Geodesic operators of Section 2 built on reconstruction (Eq. 6-12).       */
+/* ------------------------------------------------------------------------ */
+
+/* Subtraction in the image's element type: the operators below produce
+ * pixel values by subtraction (the HMAX marker, DOME, RAOBJ), and a float32
+ * image holds the float32-rounded difference. f32 != 0 rounds through float
+ * arithmetic; uint8 and float64 differences are exact in double. */
+static double ora_sub(double a, double b, int f32)
+{
+    if (f32) {
+        float fa = (float)a, fb = (float)b;
+        float d = fa - fb;
+        return (double)d;
+    }
+    return a - b;
+}
+
+/* HMAX_h(f) = dilation by reconstruction of f - h under f (Eq. 6). The
+ * marker is f - h in the element type, clamped from below by `lo` (0 for
+ * uint8 images, -HUGE_VAL otherwise). */
+long oracle_hmax(const double *f, double *out, long H, long W, int conn, double h, double lo, int f32)
+{
+    long n = H * W;
+    if (n == 0) return 0;
+    double *mk = (double *)malloc((size_t)n * sizeof(double));
+    if (!mk) return -2;
+    for (long i = 0; i < n; ++i) {
+        double d = ora_sub(f[i], h, f32);
+        mk[i] = d < lo ? lo : d;
+    }
+    long r = oracle_reconstruct(mk, f, out, H, W, conn, ORA_DILATE, n + 1);
+    free(mk);
+    return r;
+}
+
+/* DOME_h(f) = f - HMAX_h(f) (Eq. 7). */
+long oracle_dome(const double *f, double *out, long H, long W, int conn, double h, double lo, int f32)
+{
+    long r = oracle_hmax(f, out, H, W, conn, h, lo, f32);
+    for (long i = 0; i < H * W; ++i) out[i] = ora_sub(f[i], out[i], f32);
+    return r;
+}
+
+/* marker equal to f on the border pixels B of the image and `fill` inside */
+static double *ora_border_marker(const double *f, long H, long W, double fill)
+{
+    double *mk = (double *)malloc((size_t)(H * W) * sizeof(double));
+    if (!mk) return NULL;
+    for (long y = 0; y < H; ++y)
+        for (long x = 0; x < W; ++x)
+            mk[y * W + x] = (y == 0 || x == 0 || y == H - 1 || x == W - 1) ? f[y * W + x] : fill;
+    return mk;
+}
+
+/* HFILL(f) = erosion by reconstruction of m_HFILL under f, m_HFILL = f on
+ * the border and max f inside (Eq. 8-9). */
+long oracle_hfill(const double *f, double *out, long H, long W, int conn)
+{
+    long n = H * W;
+    if (n == 0) return 0;
+    double mx = f[0];
+    for (long i = 1; i < n; ++i) if (f[i] > mx) mx = f[i];
+    double *mk = ora_border_marker(f, H, W, mx);
+    if (!mk) return -2;
+    long r = oracle_reconstruct(mk, f, out, H, W, conn, ORA_ERODE, n + 1);
+    free(mk);
+    return r;
+}
+
+/* RAOBJ(f) = f - dilation by reconstruction of m_RAOBJ under f, m_RAOBJ = f
+ * on the border and min f inside (Eq. 10-11). */
+long oracle_raobj(const double *f, double *out, long H, long W, int conn, int f32)
+{
+    long n = H * W;
+    if (n == 0) return 0;
+    double mn = f[0];
+    for (long i = 1; i < n; ++i) if (f[i] < mn) mn = f[i];
+    double *mk = ora_border_marker(f, H, W, mn);
+    if (!mk) return -2;
+    long r = oracle_reconstruct(mk, f, out, H, W, conn, ORA_DILATE, n + 1);
+    for (long i = 0; i < n; ++i) out[i] = ora_sub(f[i], out[i], f32);
+    free(mk);
+    return r;
+}
+
+/* Opening by reconstruction gamma_rec^s(f) = dilation by reconstruction of
+ * eps_s(f) under f (Eq. 12). */
+long oracle_open_rec(const double *f, double *out, long H, long W, int conn, long s)
+{
+    long n = H * W;
+    if (n == 0) return 0;
+    double *mk = (double *)malloc((size_t)n * sizeof(double));
+    if (!mk) return -2;
+    if (oracle_window(f, mk, H, W, s, ORA_ERODE) != 0) { free(mk); return -2; }
+    long r = oracle_reconstruct(mk, f, out, H, W, conn, ORA_DILATE, n + 1);
+    free(mk);
+    return r;
+}

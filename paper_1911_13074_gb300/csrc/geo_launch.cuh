@@ -43,17 +43,24 @@ static void *rr_kernel_ptr(int op, int conn) {
 template <template <int> class RP>
 static int launch_rr_impl(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid) {
   void *k = rr_kernel_ptr<RP>(op, conn);
+  const size_t smem = rr_smem_bytes<RP<DILATE>>();
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return GEO_ERR_CUDA;
   TileLaunch arg = L;
   void *args[] = {(void *)&arg};
-  cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(grid), dim3(RP<DILATE>::NW * 32), args, 0, s);
+  cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(grid), dim3(RP<DILATE>::NW * 32), args, smem, s);
   return e == cudaSuccess ? GEO_OK : GEO_ERR_CUDA;
 }
 
 template <template <int> class RP>
 static int occupancy_rr_impl(int op, int conn, int *bps) {
   void *k = rr_kernel_ptr<RP>(op, conn);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, RP<DILATE>::NW * 32, 0) == cudaSuccess ? GEO_OK
-                                                                                                      : GEO_ERR_CUDA;
+  const size_t smem = rr_smem_bytes<RP<DILATE>>();
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return GEO_ERR_CUDA;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, RP<DILATE>::NW * 32, smem) == cudaSuccess
+             ? GEO_OK
+             : GEO_ERR_CUDA;
 }
 
 }  // namespace geo

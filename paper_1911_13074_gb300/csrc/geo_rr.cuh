@@ -428,12 +428,21 @@ __device__ __forceinline__ bool wait_neighbours(const int *epoch, int ty, int tx
   return true;
 }
 
+template <class P>
+constexpr size_t rr_smem_bytes() {
+  return sizeof(typename P::Wd) * 2 * (P::NW + 2) * 2 * 32 * P::CW;
+}
+
 template <class P, int CONN>
 __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
   using R = RR<P>;
   using Wd = typename P::Wd;
   constexpr int CW = R::CW, RW = R::RW, NW = R::NW, PH = R::PH, RWID = R::RWID;
-  __shared__ __align__(16) Wd xbuf[2][NW + 2][2][RWID];
+  // boundary-row exchange buffer [parity][warp slot][top/bottom][column], in
+  // dynamic shared memory (rr_smem_bytes) because with many warps it exceeds
+  // the 48 KB of static shared memory
+  extern __shared__ __align__(16) char rr_dyn[];
+  Wd(*xbuf)[NW + 2][2][RWID] = reinterpret_cast<Wd(*)[NW + 2][2][RWID]>(rr_dyn);
   __shared__ int changed_s;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int K = L.K, TH = L.TH, TW = L.TW;

@@ -8,6 +8,7 @@ import tempfile
 import pytest
 
 import oracle
+from tests import test_oracle_ops_pins as ops_pins
 from tests import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
@@ -37,6 +38,13 @@ MUTANTS = [
     ("gather_transposed", "long py = y - dy, px = x - dx;", "long py = y + dy, px = x + dx;"),
     ("gmask_overwrites", "if (to_mask) gmask[y * W + x] += gmarker[y * W + x];",
      "if (to_mask) gmask[y * W + x] = gmarker[y * W + x];"),
+    ("hmax_no_floor", "mk[i] = d < lo ? lo : d;", "mk[i] = d;"),
+    ("hmax_adds_h", "double d = ora_sub(f[i], h, f32);", "double d = ora_sub(f[i], -h, f32);"),
+    ("hfill_uses_min", "for (long i = 1; i < n; ++i) if (f[i] > mx) mx = f[i];",
+     "for (long i = 1; i < n; ++i) if (f[i] < mx) mx = f[i];"),
+    ("border_misses_last_column", "(y == 0 || x == 0 || y == H - 1 || x == W - 1)", "(y == 0 || x == 0 || y == H - 1)"),
+    ("open_rec_dilates", "if (oracle_window(f, mk, H, W, s, ORA_ERODE) != 0)",
+     "if (oracle_window(f, mk, H, W, s, ORA_DILATE) != 0)"),
 ]
 
 PIN_TESTS = [
@@ -51,6 +59,12 @@ PIN_TESTS = [
     lambda: pins.test_backward_source_identity(4, "erode"),
     lambda: pins.test_backward_tie_rule_lowest_index_and_marker_on_mask_tie(),
     lambda: pins.test_backward_erosion_tie_rule(),
+    lambda: ops_pins.test_hfill_binary_is_fill_holes(8),
+    lambda: ops_pins.test_raobj_binary_removes_border_components(4),
+    lambda: ops_pins.test_open_rec_binary_keeps_components_meeting_the_erosion(8),
+    lambda: ops_pins.test_hmax_is_widest_path_of_shifted_marker(8, "u8"),
+    lambda: ops_pins.test_hmax_flattens_peaks_lower_than_h(),
+    lambda: ops_pins.test_hmax_of_image_lower_than_h(),
 ]
 
 
