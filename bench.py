@@ -273,6 +273,12 @@ def secondary(dev):
             n = int(steps_box["s"].item())
             rec[f"{kind}_{name}"] = {"ms": t * 1e3, "steps_applied": n,
                                      "gpixel_steps_per_s": mask.numel() * n / t / 1e9}
+    # geodesic operators of the paper's Table 5 on the 1024^2 u8 workload-1 image
+    g = torch.from_numpy(synth.workload1_u8()["mask"]).to(dev)
+    ops = {"hmax_h20": lambda: gm.hmax(g, 20), "dome_h20": lambda: gm.dome(g, 20), "hfill": lambda: gm.hfill(g),
+           "raobj": lambda: gm.raobj(g), "open_rec_s15": lambda: gm.open_rec(g, 15)}
+    res["operators_1024_u8"] = {"workload": "1024x1024 u8 workload-1 image, 8-connected",
+                                **{k: {"ms": _time(fn, 3) * 1e3} for k, fn in ops.items()}}
     res["reconstruct_4096"] = {
         "workload": "4096x4096 blob masks (synthetic workload 2), 8-connected dilation by reconstruction to "
                     "stability; steps_applied counts whole passes up to the first unchanged pass",

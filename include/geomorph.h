@@ -128,6 +128,34 @@ GEO_API int morph_window_erode(geo_dtype dtype, const void *in, void *out, int64
                        int64_t width, int64_t pitch, int64_t half_size, void *stream);
 
 /*
+ * Geodesic operators of Section 2 built on reconstruction. f is the input
+ * image (also the mask of the reconstruction), out the result; out must not
+ * overlap f. Values that the operators produce by subtraction are computed in
+ * the element type (uint8 saturates at 0; float32 rounds to float32).
+ * geo_hmax      HMAX_h(f) = delta_rec^f(f - h)            (Eq. 6), h >= 0
+ *               (uint8: h rounded down, at most 255)
+ * geo_dome      DOME_h(f) = f - HMAX_h(f)                 (Eq. 7)
+ * geo_hfill     HFILL(f) = eps_rec^f(m), m = f on the image border and
+ *               max f inside                              (Eq. 8-9)
+ * geo_raobj     RAOBJ(f) = f - delta_rec^f(m), m = f on the border and
+ *               min f inside                              (Eq. 10-11)
+ * geo_open_rec  gamma_rec^s(f) = delta_rec^f(eps_s(f)), eps_s the clipped
+ *               (2s+1)^2 square erosion                   (Eq. 12)
+ * conn (4 or 8) is the connectivity of the reconstruction. Asynchronous on
+ * stream; device-side non-convergence is reported by geo_device_status.
+ */
+GEO_API int geo_hmax(geo_dtype dtype, const void *f, void *out, int64_t height, int64_t width, int64_t pitch,
+             int conn, double h, void *stream);
+GEO_API int geo_dome(geo_dtype dtype, const void *f, void *out, int64_t height, int64_t width, int64_t pitch,
+             int conn, double h, void *stream);
+GEO_API int geo_hfill(geo_dtype dtype, const void *f, void *out, int64_t height, int64_t width, int64_t pitch,
+              int conn, void *stream);
+GEO_API int geo_raobj(geo_dtype dtype, const void *f, void *out, int64_t height, int64_t width, int64_t pitch,
+              int conn, void *stream);
+GEO_API int geo_open_rec(geo_dtype dtype, const void *f, void *out, int64_t height, int64_t width,
+                 int64_t pitch, int conn, int64_t half_size, void *stream);
+
+/*
  * Batched execution: many independent items in one persistent launch.
  * The paper has no batched form; item i computes exactly what the matching
  * single-item entry point computes on its own images.

@@ -26,6 +26,7 @@ __all__ = [
     "GeoError", "load", "library_path", "dilate_chain", "erode_chain", "reconstruct",
     "window_dilate", "window_erode", "device_status", "DTYPES", "geodesic_chain",
     "chain_fwd_ckpt", "chain_backward", "Batch", "OPS", "autotune", "tune_load", "tune_lookup", "plan_info",
+    "hmax", "dome", "hfill", "raobj", "open_rec",
 ]
 
 GEO_U8, GEO_F32, GEO_F64 = 0, 1, 2
@@ -110,6 +111,15 @@ def load():
         lib.geo_tune_load.restype = I
         lib.geo_tune_lookup.argtypes = [I, I, I, L, L, L]
         lib.geo_tune_lookup.restype = I
+        D = ctypes.c_double
+        for name in ("geo_hmax", "geo_dome"):
+            getattr(lib, name).argtypes = [I, P, P, L, L, L, I, D, P]
+            getattr(lib, name).restype = I
+        for name in ("geo_hfill", "geo_raobj"):
+            getattr(lib, name).argtypes = [I, P, P, L, L, L, I, P]
+            getattr(lib, name).restype = I
+        lib.geo_open_rec.argtypes = [I, P, P, L, L, L, I, L, P]
+        lib.geo_open_rec.restype = I
         IPtr = ctypes.POINTER(I)
         lib.geo_plan_info.argtypes = [I, I, I, L, L, L, IPtr, IPtr, IPtr]
         lib.geo_plan_info.restype = I
@@ -426,3 +436,44 @@ def plan_info(dtype, op, conn, height, width, steps):
     _check(load().geo_plan_info(dt, code, int(conn), int(height), int(width), int(steps), ctypes.byref(K),
                                 ctypes.byref(TH), ctypes.byref(TW)), "geo_plan_info")
     return K.value, TH.value, TW.value
+
+
+# ---------------------------------------------------------------------------
+# geodesic operators (Section 2, Eq. 6-12)
+# ---------------------------------------------------------------------------
+
+def _op(name, f, conn, *extra, out=None):
+    lib = load()
+    _image(f, "f")
+    out = _out_like(f, out)
+    H, W = f.shape
+    with torch.cuda.device(f.device):
+        rc = getattr(lib, name)(DTYPES[f.dtype], f.data_ptr(), out.data_ptr(), H, W, _pitch(f), int(conn), *extra,
+                                _stream(f))
+    _check(rc, name)
+    return out
+
+
+def hmax(f, h, conn=8, out=None):
+    """HMAX_h(f) = delta_rec^f(f - h) (Eq. 6)."""
+    return _op("geo_hmax", f, conn, float(h), out=out)
+
+
+def dome(f, h, conn=8, out=None):
+    """DOME_h(f) = f - HMAX_h(f) (Eq. 7)."""
+    return _op("geo_dome", f, conn, float(h), out=out)
+
+
+def hfill(f, conn=8, out=None):
+    """HFILL(f): hole filling, erosion by reconstruction from the border (Eq. 8-9)."""
+    return _op("geo_hfill", f, conn, out=out)
+
+
+def raobj(f, conn=8, out=None):
+    """RAOBJ(f): removal of objects touching the border (Eq. 10-11)."""
+    return _op("geo_raobj", f, conn, out=out)
+
+
+def open_rec(f, half_size, conn=8, out=None):
+    """gamma_rec^s(f) = delta_rec^f(eps_s(f)), opening by reconstruction (Eq. 12)."""
+    return _op("geo_open_rec", f, conn, int(half_size), out=out)

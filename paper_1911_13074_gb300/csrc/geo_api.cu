@@ -52,6 +52,15 @@ static int device_state(DeviceState **out) {
   return GEO_OK;
 }
 
+int pool_alloc(void **p, size_t n, cudaStream_t s) {
+  DeviceState *ds = nullptr;
+  const int rc = device_state(&ds);
+  if (rc != GEO_OK) return rc;
+  return cudaMallocFromPoolAsync(p, n, ds->pool, s) == cudaSuccess ? GEO_OK : GEO_ERR_CUDA;
+}
+
+int pool_free(void *p, cudaStream_t s) { return cudaFreeAsync(p, s) == cudaSuccess ? GEO_OK : GEO_ERR_CUDA; }
+
 int device_status_word(int **status) {
   DeviceState *ds = nullptr;
   const int rc = device_state(&ds);

@@ -82,6 +82,10 @@ struct Plan {
 // the tune cache has no entry (geo_tune.cu).
 int tuned_k(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps);
 
+// Stream-ordered scratch from the library's per-device pool (geo_api.cu).
+int pool_alloc(void **p, size_t n, cudaStream_t s);
+int pool_free(void *p, cudaStream_t s);
+
 // The per-device status word that device-side waits report into (geo_api.cu).
 int device_status_word(int **status);
 
