@@ -120,6 +120,30 @@ def measured_peaks():
         return {}
 
 
+def kernel_source_sha256():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1911_13074_gb300", "csrc", "*.cu*"))):
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the chain kernel from the committed ncu record,
+    or None when the kernel sources changed since the counters were taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "rr_kernel_u8_1024_chain1500_traffic.json")) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_sha256") != kernel_source_sha256():
+        return None
+    return rec.get("traffic_bytes_per_launch")
+
+
 def alu_peak_top_s(nsm, mhz):
     """Peak exact min/max rate for uint8 pixels, in tera pixel-ops per second.
 
@@ -387,7 +411,8 @@ def main():
                 "d2h_bytes_per_step": H * W},
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tpixel-op/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": measured_traffic(),
+                     "traffic_unit": "bytes per launch (dram read + write, ncu)",
                      "peak_basis": f"{nsm} SMs x 128 lanes/clk x 2 px (max.u16x2) x {sm_max:.0f} MHz",
                      "ops_per_pixel_step": OPS_PER_PX_STEP},
     }
