@@ -356,7 +356,8 @@ int run_chain(int dt, const void *marker, const void *mask, void *out, int64_t H
   // and one ping-pong image with a 16-byte aligned pitch
   const int64_t spitch_b = ((W * es + 15) / 16) * 16;
   const size_t ntiles = (size_t)P.tiles_x * (size_t)P.tiles_y * (size_t)batch;
-  const size_t ctl_b = 256 + ((ntiles * sizeof(int) + 255) / 256) * 256;
+  // [control 256 B][per-tile pass epochs][per-tile changed flags, two passes]
+  const size_t ctl_b = 256 + ((3 * ntiles * sizeof(int) + 255) / 256) * 256;
   const size_t scratch_b = ctl_b + (size_t)spitch_b * (size_t)H * (size_t)batch;
   void *scratch = nullptr;
   if (cudaMallocFromPoolAsync(&scratch, scratch_b, ds->pool, s) != cudaSuccess) return GEO_ERR_CUDA;
@@ -386,6 +387,7 @@ int run_chain(int dt, const void *marker, const void *mask, void *out, int64_t H
   L.alias = alias ? 1 : 0;
   L.ctl = (Control *)scratch;
   L.epoch = (int *)((char *)scratch + 256);
+  L.tchg = L.epoch + ntiles;
   L.status = ds->status;
   L.steps_out = steps_out;
   if (mode == MODE_CHAIN) {

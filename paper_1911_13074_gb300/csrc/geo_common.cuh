@@ -69,6 +69,7 @@ struct TileLaunch {
   int64_t *steps_out;     // rec: optional device pointer
   int batch;              // images of equal shape, one after another (<= 1: one image)
   int *epoch;             // register kernel, chains: per tile, passes completed
+  int *tchg;              // register kernel, reconstruction: [2][tiles] changed flags per pass
 };
 
 // Tile geometry of one launch: interior TH x TW, halo K, shared-memory row

@@ -428,6 +428,21 @@ __device__ __forceinline__ bool wait_neighbours(const int *epoch, int ty, int tx
   return true;
 }
 
+// Whether any tile of the 3x3 tile neighbourhood of (ty, tx) has a non-zero
+// flag (flags of one image, the previous pass).
+__device__ __forceinline__ int any_neighbour_changed(const int *flags, int ty, int tx, int tiles_y, int tiles_x) {
+  for (int dy = -1; dy <= 1; ++dy) {
+    const int ny = ty + dy;
+    if (ny < 0 || ny >= tiles_y) continue;
+    for (int dx = -1; dx <= 1; ++dx) {
+      const int nx = tx + dx;
+      if (nx < 0 || nx >= tiles_x) continue;
+      if (__ldcg(flags + ny * tiles_x + nx)) return 1;
+    }
+  }
+  return 0;
+}
+
 template <class P>
 constexpr size_t rr_smem_bytes() {
   return sizeof(typename P::Wd) * 2 * (P::NW + 2) * 2 * 32 * P::CW;
@@ -443,7 +458,7 @@ __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
   // the 48 KB of static shared memory
   extern __shared__ __align__(16) char rr_dyn[];
   Wd(*xbuf)[NW + 2][2][RWID] = reinterpret_cast<Wd(*)[NW + 2][2][RWID]>(rr_dyn);
-  __shared__ int changed_s;
+  __shared__ int changed_s, active_s;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int K = L.K, TH = L.TH, TW = L.TW;
   const int tiles_img = L.tiles_x * L.tiles_y;
@@ -496,15 +511,38 @@ __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
           record_status(L.status, GEO_ERR_TIMEOUT);
         __syncthreads();
       }
+      int steps_here = S;
+      if (rec && pass >= 1) {
+        // Work-efficient reconstruction: if no tile of this tile's 3x3 tile
+        // neighbourhood changed in the previous pass, this tile's region is
+        // what it was one pass ago, so this pass cannot change it either
+        // (the chain is monotone from its first step on). From pass 2 on both
+        // ping-pong buffers already hold its current interior and it is
+        // skipped; in pass 1 the second buffer is still unwritten, so the
+        // interior is copied without steps.
+        const int *prev = L.tchg + (size_t)((pass - 1) & 1) * ntiles + (size_t)bi * tiles_img;
+        if (threadIdx.x == 0) active_s = any_neighbour_changed(prev, ty, tx, L.tiles_y, L.tiles_x);
+        __syncthreads();
+        if (!active_s) {
+          if (threadIdx.x == 0) L.tchg[(size_t)(pass & 1) * ntiles + t] = 0;
+          if (pass >= 2) continue;
+          steps_here = 0;
+        }
+      }
       R::load_words(src, L.H, L.W, gy0, gx, src_cg, false, w);
       if (!mask_resident || pass == 0) R::load_words(mask, L.H, L.W, gy0, gx, false, virt, m);
       bool ok = true;
-      for (int j = 0; j < S; ++j) {
+      for (int j = 0; j < steps_here; ++j) {
         ok &= R::template step<CONN>(w, m, &xbuf[parity][0][0][0], &xbar, parity, lane, warp);
         parity ^= 1;
       }
       if (!ok) record_status(L.status, GEO_ERR_TIMEOUT);
-      changed |= R::store(w, dst, src, rec, L.H, L.W, ty0, tx0, K, TH, TW, lane, warp);
+      const bool tile_changed = R::store(w, dst, src, rec, L.H, L.W, ty0, tx0, K, TH, TW, lane, warp);
+      changed |= tile_changed;
+      if (rec) {
+        const int any = __syncthreads_or(tile_changed ? 1 : 0);
+        if (threadIdx.x == 0) L.tchg[(size_t)(pass & 1) * ntiles + t] = any;
+      }
       if (!rec && pass + 1 < L.npasses) {
         __syncthreads();  // every thread's stores of this tile are issued
         if (threadIdx.x == 0) {
