@@ -66,6 +66,17 @@ struct RU8 {
     v[2] = u.z;
     v[3] = u.w;
   }
+  // one lane's CW pixels of one row as loaded from global memory
+  using Raw = uint32_t;
+  __device__ static Raw load_raw(const char *p, bool cg) {
+    return cg ? __ldcg(reinterpret_cast<const unsigned int *>(p)) : __ldg(reinterpret_cast<const unsigned int *>(p));
+  }
+  __device__ static void unpack_raw(Raw x, Px (&v)[CW]) {
+    v[0] = x & 0xffu;
+    v[1] = (x >> 8) & 0xffu;
+    v[2] = (x >> 16) & 0xffu;
+    v[3] = x >> 24;
+  }
   // CW = 4 consecutive pixels from global memory (one 4-byte access)
   __device__ static void load_vec(const char *p, bool cg, Px (&v)[CW]) {
     const uint32_t x = cg ? __ldcg(reinterpret_cast<const unsigned int *>(p))
@@ -110,6 +121,16 @@ struct RF32 {
     v[2] = __uint_as_float(u.z);
     v[3] = __uint_as_float(u.w);
   }
+  using Raw = float4;
+  __device__ static Raw load_raw(const char *p, bool cg) {
+    return cg ? __ldcg(reinterpret_cast<const float4 *>(p)) : __ldg(reinterpret_cast<const float4 *>(p));
+  }
+  __device__ static void unpack_raw(Raw x, Px (&v)[CW]) {
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = x.z;
+    v[3] = x.w;
+  }
   __device__ static void load_vec(const char *p, bool cg, Px (&v)[CW]) {
     const float4 x = cg ? __ldcg(reinterpret_cast<const float4 *>(p)) : __ldg(reinterpret_cast<const float4 *>(p));
     v[0] = x.x;
@@ -152,6 +173,14 @@ struct RF64 {
   __device__ static void unpack(uint4 u, Wd (&v)[CW]) {
     v[0] = (long long)(((unsigned long long)u.y << 32) | u.x);
     v[1] = (long long)(((unsigned long long)u.w << 32) | u.z);
+  }
+  using Raw = longlong2;
+  __device__ static Raw load_raw(const char *p, bool cg) {
+    return cg ? __ldcg(reinterpret_cast<const longlong2 *>(p)) : __ldg(reinterpret_cast<const longlong2 *>(p));
+  }
+  __device__ static void unpack_raw(Raw x, Px (&v)[CW]) {
+    v[0] = f64_key(__longlong_as_double(x.x));
+    v[1] = f64_key(__longlong_as_double(x.y));
   }
   __device__ static void load_vec(const char *p, bool cg, Px (&v)[CW]) {
     const longlong2 x =
@@ -251,6 +280,28 @@ struct RR {
 
   __device__ static void load_words(const Plane &Q, int64_t H, int64_t W, int64_t gy0, int64_t gx, bool cg,
                                     bool virt, Wd (&w)[RW][CW]) {
+    if (!virt && Q.vec_ok && gy0 >= 0 && gy0 + B * RW <= H && gx >= 0 && gx + CW <= W) {
+      // the lane's strip lies inside the image: issue every row's load
+      // before using any, so they are in flight together
+      typename P::Raw raw[B * RW];
+      const char *base = Q.ptr + gy0 * Q.pitch_b + gx * GS;
+#pragma unroll
+      for (int i = 0; i < B * RW; ++i) raw[i] = P::load_raw(base + i * Q.pitch_b, cg);
+#pragma unroll
+      for (int r = 0; r < RW; ++r) {
+        Px lo[CW], hi[CW];
+        P::unpack_raw(raw[r], lo);
+        if constexpr (B == 2) {
+          P::unpack_raw(raw[RW + r], hi);
+        } else {
+#pragma unroll
+          for (int c = 0; c < CW; ++c) hi[c] = lo[c];
+        }
+#pragma unroll
+        for (int c = 0; c < CW; ++c) w[r][c] = P::make(lo[c], hi[c]);
+      }
+      return;
+    }
 #pragma unroll
     for (int r = 0; r < RW; ++r) {
       Px lo[CW], hi[CW];
@@ -407,25 +458,29 @@ struct RR {
 };
 
 // Wait until every tile of the 3x3 tile neighbourhood of (ty, tx) has
-// published epoch >= want. Bounded; false if the wait expired.
+// published epoch >= want. Called by all lanes of one warp: lane k < 9 polls
+// neighbour k, so the eight acquire loads are in flight together instead of
+// one after another. Bounded; false (on every lane) if a wait expired.
 __device__ __forceinline__ bool wait_neighbours(const int *epoch, int ty, int tx, int tiles_y, int tiles_x,
-                                                int want) {
-  const unsigned long long t0 = globaltimer_ns();
-  for (int dy = -1; dy <= 1; ++dy) {
-    const int ny = ty + dy;
-    if (ny < 0 || ny >= tiles_y) continue;
-    for (int dx = -1; dx <= 1; ++dx) {
-      const int nx = tx + dx;
-      if (nx < 0 || nx >= tiles_x || (dx == 0 && dy == 0)) continue;
+                                                int want, int lane) {
+  bool ok = true;
+  if (lane < 9 && lane != 4) {
+    const int ny = ty + lane / 3 - 1, nx = tx + lane % 3 - 1;
+    if (ny >= 0 && ny < tiles_y && nx >= 0 && nx < tiles_x) {
       const unsigned *f = reinterpret_cast<const unsigned *>(epoch) + ny * tiles_x + nx;
+      const unsigned long long t0 = globaltimer_ns();
       unsigned spins = 0;
       while ((int)ld_acquire_u32(f) < want) {
-        if ((++spins & 255u) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) return false;
+        if ((++spins & 255u) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) {
+          ok = false;
+          break;
+        }
       }
     }
   }
-  __threadfence();
-  return true;
+  // the acquire loads, followed by the caller's CTA barrier, order every
+  // thread's later loads of the neighbours' tiles after their stores
+  return __all_sync(0xffffffffu, ok);
 }
 
 // Whether any tile of the 3x3 tile neighbourhood of (ty, tx) has a non-zero
@@ -507,7 +562,9 @@ __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
         // chains synchronise point to point: the tiles whose interiors this
         // tile's halo reads must have finished the previous pass (which also
         // means they are done reading the buffer this pass overwrites)
-        if (threadIdx.x == 0 && !wait_neighbours(L.epoch + (size_t)bi * tiles_img, ty, tx, L.tiles_y, L.tiles_x, pass))
+        if (warp == 0 &&
+            !wait_neighbours(L.epoch + (size_t)bi * tiles_img, ty, tx, L.tiles_y, L.tiles_x, pass, lane) &&
+            lane == 0)
           record_status(L.status, GEO_ERR_TIMEOUT);
         __syncthreads();
       }
@@ -544,11 +601,11 @@ __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
         if (threadIdx.x == 0) L.tchg[(size_t)(pass & 1) * ntiles + t] = any;
       }
       if (!rec && pass + 1 < L.npasses) {
-        __syncthreads();  // every thread's stores of this tile are issued
-        if (threadIdx.x == 0) {
-          __threadfence();
-          st_release_u32(reinterpret_cast<unsigned *>(L.epoch) + t, (unsigned)(pass + 1));
-        }
+        // every thread's stores of this tile happen before the barrier, and
+        // the barrier before thread 0's release store, so the release (which
+        // is cumulative) publishes the whole tile at gpu scope
+        __syncthreads();
+        if (threadIdx.x == 0) st_release_u32(reinterpret_cast<unsigned *>(L.epoch) + t, (unsigned)(pass + 1));
       }
     }
     if (rec) {
@@ -562,8 +619,7 @@ __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
       steps_left -= S;
     } else {
       if (pass == L.npasses - 1) break;
-      if (*(volatile int *)L.status != 0) return;
-      continue;  // no grid barrier between chain passes
+      continue;  // no grid barrier between chain passes (every wait is bounded)
     }
     if (!grid_barrier(L.ctl, L.status, gridDim.x)) return;
     if (rec) {
