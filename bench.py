@@ -144,6 +144,26 @@ def measured_traffic():
     return rec.get("traffic_bytes_per_launch")
 
 
+def max_over_ranks(values, world, device=None):
+    """Per-rank timings -> their maximum over all ranks (the slowest rank
+    sets the whole job's time). One all-reduce on the process group's
+    backend: CUDA tensors under NCCL, CPU tensors under gloo."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    dev = device if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def whole_job_rate(world, units_per_rank_step, steps, seconds):
+    """Units all ranks processed (weak scaling: each rank a full workload per
+    step) per second, in billions."""
+    return world * units_per_rank_step * steps / seconds / 1e9
+
+
 def alu_peak_top_s(nsm, mhz):
     """Peak exact min/max rate for uint8 pixels, in tera pixel-ops per second.
 
@@ -315,6 +335,9 @@ def main():
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
         return
     import numpy as np
     import torch
@@ -380,17 +403,16 @@ def main():
     barrier()
     t_e2e = e0.elapsed_time(e1) / 1e3
 
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev, t_e2e = float(tt[0]), float(tt[1])
+    t_dev, t_e2e = max_over_ranks([t_dev, t_e2e], world, dev)
     if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
         return
 
     px_steps = H * W * CHAIN_STEPS
-    value = world * px_steps * args.steps / t_dev / 1e9
-    e2e_value = world * px_steps * args.steps / t_e2e / 1e9
+    value = whole_job_rate(world, px_steps, args.steps, t_dev)
+    e2e_value = whole_job_rate(world, px_steps, args.steps, t_e2e)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
