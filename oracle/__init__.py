@@ -76,6 +76,10 @@ def _load():
             lib.oracle_raobj.restype = L
             lib.oracle_open_rec.argtypes = [P, P, L, L, I, L]
             lib.oracle_open_rec.restype = L
+            lib.oracle_qdt_residual.argtypes = [P, P, P, L, L, I, L]
+            lib.oracle_qdt_residual.restype = I
+            lib.oracle_qdt_lipschitz.argtypes = [P, P, L, L, I, L]
+            lib.oracle_qdt_lipschitz.restype = L
             _lib = lib
     return _lib
 
@@ -89,7 +93,7 @@ def use_library(path):
     lib = ctypes.CDLL(path)
     for name in ("oracle_step", "oracle_chain", "oracle_reconstruct", "oracle_window",
                  "oracle_chain_backward", "oracle_hmax", "oracle_dome", "oracle_hfill", "oracle_raobj",
-                 "oracle_open_rec"):
+                 "oracle_open_rec", "oracle_qdt_residual", "oracle_qdt_lipschitz"):
         fn, ref = getattr(lib, name), getattr(prev, name)
         fn.argtypes, fn.restype = ref.argtypes, ref.restype
     with _lock:
@@ -238,3 +242,55 @@ def raobj(f, conn=8):
 def open_rec(f, s, conn=8):
     """gamma_rec^s(f) = delta_rec^f(eps_s(f)) (Eq. 12)."""
     return _op_call("oracle_open_rec", f, conn, int(s))
+
+
+# ---------------------------------------------------------------------------
+# quasi-distance transform (Section 2, Eq. 13-15; Algorithm 6)
+# ---------------------------------------------------------------------------
+
+def qdt_steps(H, W, conn=8):
+    """Number of eps_1 erosions after which eps_j(f) is constant on an H x W
+    image: the clipped square of half size max(H, W) - 1 (the cross of radius
+    H + W - 2) covers the whole image from every pixel."""
+    if H == 0 or W == 0:
+        return 0
+    return max(H, W) - 1 if conn == 8 else H + W - 2
+
+
+def qdt_residual(f, conn=8, steps=None):
+    """d(f) of Eq. 13 as Algorithm 6 computes it. Returns (r, d): the largest
+    residual eps_{j-1}(f) - eps_j(f) over the erosions j = 1..steps (f's dtype)
+    and the first j that attains it (int32; 0 where no erosion lowers the
+    pixel)."""
+    lib = _load()
+    f64 = _f64(f)
+    H, W = f64.shape
+    if steps is None:
+        steps = qdt_steps(H, W, conn)
+    r = np.empty_like(f64)
+    d = np.empty_like(f64)
+    if lib.oracle_qdt_residual(_ptr(f64), _ptr(r), _ptr(d), H, W, conn, int(steps)) != 0:
+        raise MemoryError("oracle_qdt_residual failed")
+    return _back(r, np.asarray(f)), d.astype(np.int32)
+
+
+def qdt_lipschitz(g, conn=8, max_steps=None):
+    """The limit of eta (Eq. 14-15) applied to g. Returns (out int32, changing
+    steps)."""
+    lib = _load()
+    g64 = _f64(g)
+    H, W = g64.shape
+    out = np.empty_like(g64)
+    if max_steps is None:
+        max_steps = H * W + 1
+    n = lib.oracle_qdt_lipschitz(_ptr(g64), _ptr(out), H, W, conn, int(max_steps))
+    if n == -2:
+        raise MemoryError("oracle_qdt_lipschitz failed")
+    return out.astype(np.int32), int(n)
+
+
+def qdt(f, conn=8):
+    """Quasi-distance transform: (r, d, d_L1) with d_L1 the eta limit of d."""
+    r, d = qdt_residual(f, conn)
+    dl1, _ = qdt_lipschitz(d, conn)
+    return r, d, dl1

@@ -14,6 +14,9 @@
  *   Section 2, Eq. 4    geodesic erosion/dilation of size s = s nested steps
  *   Section 2, Eq. 5    reconstruction = the limit of the chain (iterate until
  *                       a step changes nothing, as in Section 3.7, Algorithm 5)
+ *   Section 2, Eq. 6-12 geodesic operators built on reconstruction
+ *   Section 2, Eq. 13-15 quasi-distance transform (residuals of an erosion
+ *                       chain as in Algorithm 6, then the eta iteration)
  *
  * Every value is held as a double. uint8 and float32 images convert to double
  * exactly, and the forward operators only select among their inputs, so the
@@ -324,4 +327,69 @@ long oracle_open_rec(const double *f, double *out, long H, long W, int conn, lon
     long r = oracle_reconstruct(mk, f, out, H, W, conn, ORA_DILATE, n + 1);
     free(mk);
     return r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Quasi-distance transform (Section 2, Eq. 13-15; Section 3.8, Algorithm 6) */
+/* ------------------------------------------------------------------------ */
+
+/* First part, d(f) of Eq. 13 as Algorithm 6 builds it: erode f over and over
+ * with eps_1; after the j-th erosion (j = 1, 2, ...) the residual
+ * eps_{j-1}(f) - eps_j(f) of each pixel is compared with the largest residual
+ * r kept so far and, where it is strictly larger, it replaces r and j
+ * replaces d. r and d start at 0: a pixel whose value never drops keeps
+ * d = 0, and a residual equal to an earlier one keeps the earlier j.
+ * `steps` erosions are applied; once eps_j(f) is constant (j >= max(H, W) - 1
+ * for the square, H + W - 2 for the cross) every later residual is 0. */
+int oracle_qdt_residual(const double *f, double *r, double *d, long H, long W, int conn, long steps)
+{
+    long n = H * W;
+    if (n == 0) return 0;
+    double *cur = (double *)malloc((size_t)n * sizeof(double));
+    double *nxt = (double *)malloc((size_t)n * sizeof(double));
+    if (!cur || !nxt) { free(cur); free(nxt); return -1; }
+    memcpy(cur, f, (size_t)n * sizeof(double));
+    for (long i = 0; i < n; ++i) { r[i] = 0.0; d[i] = 0.0; }
+    for (long j = 1; j <= steps; ++j) {
+        oracle_step(cur, NULL, nxt, H, W, conn, ORA_ERODE);
+        for (long i = 0; i < n; ++i) {
+            double res = cur[i] - nxt[i];
+            if (res > r[i]) { r[i] = res; d[i] = (double)j; }
+        }
+        double *t = cur; cur = nxt; nxt = t;
+    }
+    free(cur);
+    free(nxt);
+    return 0;
+}
+
+/* Second part: eta of Eq. 14, applied until a step changes nothing (the
+ * limit of Eq. 15). eta(g)(p) = eps_1(g)(p) + 1 where g(p) - eps_1(g)(p) > 1
+ * and g(p) elsewhere; each step computes every pixel from the whole previous
+ * image. Returns the number of steps that changed something, -1 if max_steps
+ * steps all did, -2 on allocation failure. */
+long oracle_qdt_lipschitz(const double *g, double *out, long H, long W, int conn, long max_steps)
+{
+    long n = H * W;
+    if (n == 0) return 0;
+    double *eps = (double *)malloc((size_t)n * sizeof(double));
+    double *tmp = (double *)malloc((size_t)n * sizeof(double));
+    if (!eps || !tmp) { free(eps); free(tmp); return -2; }
+    memcpy(out, g, (size_t)n * sizeof(double));
+    long changing = 0;
+    for (;;) {
+        if (changing >= max_steps) { changing = -1; break; }
+        oracle_step(out, NULL, eps, H, W, conn, ORA_ERODE);
+        int changed = 0;
+        for (long i = 0; i < n; ++i) {
+            tmp[i] = (out[i] - eps[i] > 1.0) ? eps[i] + 1.0 : out[i];
+            if (tmp[i] != out[i]) changed = 1;
+        }
+        if (!changed) break;
+        memcpy(out, tmp, (size_t)n * sizeof(double));
+        ++changing;
+    }
+    free(eps);
+    free(tmp);
+    return changing;
 }

@@ -10,6 +10,7 @@ import pytest
 import oracle
 from tests import test_oracle_ops_pins as ops_pins
 from tests import test_oracle_pins as pins
+from tests import test_oracle_qdt_pins as qdt_pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
 
@@ -45,6 +46,17 @@ MUTANTS = [
     ("border_misses_last_column", "(y == 0 || x == 0 || y == H - 1 || x == W - 1)", "(y == 0 || x == 0 || y == H - 1)"),
     ("open_rec_dilates", "if (oracle_window(f, mk, H, W, s, ORA_ERODE) != 0)",
      "if (oracle_window(f, mk, H, W, s, ORA_DILATE) != 0)"),
+    ("qdt_ties_take_latest", "if (res > r[i]) { r[i] = res; d[i] = (double)j; }",
+     "if (res >= r[i]) { r[i] = res; d[i] = (double)j; }"),
+    ("qdt_index_off_by_one", "if (res > r[i]) { r[i] = res; d[i] = (double)j; }",
+     "if (res > r[i]) { r[i] = res; d[i] = (double)(j - 1); }"),
+    ("qdt_skips_last_erosion", "for (long j = 1; j <= steps; ++j) {", "for (long j = 1; j < steps; ++j) {"),
+    ("qdt_residual_dilates", "oracle_step(cur, NULL, nxt, H, W, conn, ORA_ERODE);",
+     "oracle_step(cur, NULL, nxt, H, W, conn, ORA_DILATE);"),
+    ("eta_drops_plus_one", "tmp[i] = (out[i] - eps[i] > 1.0) ? eps[i] + 1.0 : out[i];",
+     "tmp[i] = (out[i] - eps[i] > 1.0) ? eps[i] : out[i];"),
+    ("eta_threshold_two", "tmp[i] = (out[i] - eps[i] > 1.0) ? eps[i] + 1.0 : out[i];",
+     "tmp[i] = (out[i] - eps[i] > 2.0) ? eps[i] + 1.0 : out[i];"),
 ]
 
 PIN_TESTS = [
@@ -65,6 +77,9 @@ PIN_TESTS = [
     lambda: ops_pins.test_hmax_is_widest_path_of_shifted_marker(8, "u8"),
     lambda: ops_pins.test_hmax_flattens_peaks_lower_than_h(),
     lambda: ops_pins.test_hmax_of_image_lower_than_h(),
+    lambda: qdt_pins.test_binary_qdt_is_the_distance_transform(8),
+    lambda: qdt_pins.test_grey_residuals_match_minimum_filters(4),
+    lambda: qdt_pins.test_lipschitz_limit_closed_form(8),
 ]
 
 
