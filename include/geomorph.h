@@ -156,6 +156,35 @@ GEO_API int geo_open_rec(geo_dtype dtype, const void *f, void *out, int64_t heig
                  int64_t pitch, int conn, int64_t half_size, void *stream);
 
 /*
+ * Quasi-distance transform (Section 2, Eq. 13-15; Section 3.8, Algorithm 6).
+ *
+ * Part 1: f is eroded S times with eps_1 (the 3x3 square for conn = 8, the
+ * cross for conn = 4; clipped to the image), S = max(H, W) - 1 (conn 8) or
+ * H + W - 2 (conn 4), after which the erosion is constant. After erosion j
+ * the residual eps_{j-1}(f) - eps_j(f) of each pixel replaces r and j
+ * replaces d where it is strictly larger than the r kept so far (r and d
+ * start at 0; equal residuals keep the earlier j).
+ * Part 2: d_l1 = the limit of eta (Eq. 14) applied to d, eta(g) =
+ * eps_1(g) + 1 where g - eps_1(g) > 1 and g elsewhere.
+ *
+ * dtype     GEO_U8 only (else GEO_ERR_DTYPE).
+ * f         device, H rows of `pitch` uint8 elements; read only.
+ * r         device uint8, same layout as f: the largest residual.
+ * d         device int32, H rows of `pitch` int32 elements: the first
+ *           erosion index attaining r (0 where no erosion lowers the pixel).
+ * d_l1      device int32 like d, or NULL to skip part 2; may equal d (then
+ *           d is overwritten by the limit).
+ * r, d and d_l1 (unless equal to d) must not overlap f or one another.
+ * Errors: GEO_ERR_ARG for negative sizes, pitch < width, conn not 4 or 8,
+ * NULL f, r or d, overlapping buffers, or S > 32766; GEO_ERR_ALIGN when d or
+ * d_l1 is not 4-byte aligned. Asynchronous on stream; a device-side wait
+ * timeout or non-convergence is reported by geo_device_status. The library
+ * allocates its scratch from its stream-ordered pool.
+ */
+GEO_API int geo_qdt(geo_dtype dtype, const void *f, void *r, int32_t *d, int32_t *d_l1, int64_t height,
+                    int64_t width, int64_t pitch, int conn, void *stream);
+
+/*
  * Batched execution: many independent items in one persistent launch.
  * The paper has no batched form; item i computes exactly what the matching
  * single-item entry point computes on its own images.

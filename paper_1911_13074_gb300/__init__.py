@@ -120,6 +120,8 @@ def load():
             getattr(lib, name).restype = I
         lib.geo_open_rec.argtypes = [I, P, P, L, L, L, I, L, P]
         lib.geo_open_rec.restype = I
+        lib.geo_qdt.argtypes = [I, P, P, P, P, L, L, L, I, P]
+        lib.geo_qdt.restype = I
         IPtr = ctypes.POINTER(I)
         lib.geo_plan_info.argtypes = [I, I, I, L, L, L, IPtr, IPtr, IPtr]
         lib.geo_plan_info.restype = I
@@ -477,3 +479,28 @@ def raobj(f, conn=8, out=None):
 def open_rec(f, half_size, conn=8, out=None):
     """gamma_rec^s(f) = delta_rec^f(eps_s(f)), opening by reconstruction (Eq. 12)."""
     return _op("geo_open_rec", f, conn, int(half_size), out=out)
+
+
+# ---------------------------------------------------------------------------
+# quasi-distance transform (Section 2, Eq. 13-15; Algorithm 6)
+# ---------------------------------------------------------------------------
+
+def qdt(f, conn=8, lipschitz=True):
+    """Quasi-distance transform of a uint8 image. Returns (r, d, d_l1): the
+    largest residual eps_{j-1}(f) - eps_j(f) over the erosion chain (uint8),
+    the first erosion j attaining it (int32, 0 where no erosion lowers the
+    pixel), and the eta limit of d (Eq. 15; None with lipschitz=False)."""
+    lib = load()
+    _image(f, "f")
+    if f.dtype != torch.uint8:
+        raise TypeError("qdt takes uint8 images")
+    H, W = f.shape
+    pitch = _pitch(f)
+    r = torch.empty_strided(f.shape, (pitch, 1), dtype=torch.uint8, device=f.device)
+    d = torch.empty_strided(f.shape, (pitch, 1), dtype=torch.int32, device=f.device)
+    dl1 = torch.empty_strided(f.shape, (pitch, 1), dtype=torch.int32, device=f.device) if lipschitz else None
+    with torch.cuda.device(f.device):
+        rc = lib.geo_qdt(DTYPES[f.dtype], f.data_ptr(), r.data_ptr(), d.data_ptr(),
+                         dl1.data_ptr() if lipschitz else None, H, W, pitch, int(conn), _stream(f))
+    _check(rc, "geo_qdt")
+    return r, d, dl1

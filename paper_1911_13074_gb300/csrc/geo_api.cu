@@ -73,7 +73,7 @@ int device_status_word(int **status) {
 // planning
 // ---------------------------------------------------------------------------
 
-static int elem_size(int dt) { return dt == GEO_U8 ? 1 : dt == GEO_F32 ? 4 : 8; }
+static int elem_size(int dt) { return dt == GEO_U8 ? 1 : (dt == GEO_F32 || dt == GEO_D32) ? 4 : 8; }
 static int chunk_elems(int dt) { return dt == GEO_U8 ? 8 : dt == GEO_F32 ? 4 : 2; }
 
 static int occupancy(int dt, int op, int conn, size_t smem, int *bps) {
@@ -193,13 +193,14 @@ struct RRGeom {
 };
 // must match SU8 / SF32 / SF64 in geo_rr.cuh (CW, RW, NW, bands)
 static RRGeom rr_geom(int dt) {
-  if (dt == GEO_U8) return RRGeom{4, GEO_RR_U8_RW, GEO_RR_U8_NW, 2};
+  if (dt == GEO_U8 || dt == GEO_D32) return RRGeom{4, GEO_RR_U8_RW, GEO_RR_U8_NW, 2};
   if (dt == GEO_F32) return RRGeom{4, GEO_RR_F32_RW, GEO_RR_F32_NW, 1};
   return RRGeom{2, GEO_RR_F64_RW, GEO_RR_F64_NW, 1};
 }
 
 static int occupancy_rr(int dt, int op, int conn, int *bps) {
   if (dt == GEO_U8) return occupancy_rr_u8(op, conn, bps);
+  if (dt == GEO_D32) return occupancy_rr_d32(op, conn, bps);
   if (dt == GEO_F32) return occupancy_rr_f32(op, conn, bps);
   return occupancy_rr_f64(op, conn, bps);
 }
@@ -287,6 +288,7 @@ static int make_plan_rr(int dt, int op, int code, int conn, int64_t H, int64_t W
 
 static int launch_rr(int dt, const TileLaunch &L, int op, int conn, cudaStream_t s, const Plan &P) {
   if (dt == GEO_U8) return launch_rr_u8(L, op, conn, s, P.grid);
+  if (dt == GEO_D32) return launch_rr_d32(L, op, conn, s, P.grid);
   if (dt == GEO_F32) return launch_rr_f32(L, op, conn, s, P.grid);
   return launch_rr_f64(L, op, conn, s, P.grid);
 }
@@ -315,11 +317,23 @@ static bool overlaps(const void *a, const void *b, size_t n) {
   return x < y + n && y < x + n;
 }
 
-// Common driver of chains, reconstruction and windows.
+int plan_rr(int dt, int op, int code, int conn, int64_t H, int64_t W, int64_t steps_hint, Plan *P) {
+  DeviceState *ds = nullptr;
+  const int rc = device_state(&ds);
+  if (rc != GEO_OK) return rc;
+  return make_plan_rr(dt, op, code, conn, H, W, steps_hint, ds->nsm, P, 1);
+}
+
+// Common driver of chains, reconstruction and windows (public element types).
 int run_chain(int dt, const void *marker, const void *mask, void *out, int64_t H, int64_t W, int64_t pitch, int conn,
               int op, int mode, int64_t steps, int64_t *steps_out, void *stream, int batch) {
-  if (batch < 1) return GEO_ERR_ARG;
   if (dt != GEO_U8 && dt != GEO_F32 && dt != GEO_F64) return GEO_ERR_DTYPE;
+  return run_chain_any(dt, marker, mask, out, H, W, pitch, conn, op, mode, steps, steps_out, stream, batch);
+}
+
+int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64_t H, int64_t W, int64_t pitch,
+                  int conn, int op, int mode, int64_t steps, int64_t *steps_out, void *stream, int batch) {
+  if (batch < 1) return GEO_ERR_ARG;
   if (H < 0 || W < 0 || pitch < W || (conn != 4 && conn != 8) || (op != DILATE && op != ERODE))
     return GEO_ERR_ARG;
   if (H == 0 || W == 0) return GEO_OK;
@@ -345,7 +359,7 @@ int run_chain(int dt, const void *marker, const void *mask, void *out, int64_t H
   int rc = device_state(&ds);
   if (rc != GEO_OK) return rc;
   const char *kern = getenv("GEOMORPH_KERNEL");
-  const bool rr = !(kern && strcmp(kern, "tile") == 0);
+  const bool rr = !(kern && strcmp(kern, "tile") == 0) || dt == GEO_D32;  // the distances have no tile kernel
   Plan P;
   const int code = mode == MODE_REC ? 2 + op : (mask ? op : 4 + op);
   rc = rr ? make_plan_rr(dt, op, code, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P, batch)

@@ -11,6 +11,10 @@ namespace geo {
 enum Op : int { DILATE = 0, ERODE = 1 };
 enum Mode : int { MODE_CHAIN = 0, MODE_REC = 1 };
 
+// Internal element type next to geo_dtype: int32 distances held as u16
+// lanes (the eta iteration of the quasi-distance transform, geo_qdt.cu).
+constexpr int GEO_D32 = 3;
+
 constexpr int kThreads = 256;  // threads per CTA of the tile kernels
 
 // Band height (word rows per warp) and warps per CTA of the single-image
@@ -98,6 +102,13 @@ int plan_tiles(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hin
 int run_chain(int dt, const void *marker, const void *mask, void *out, int64_t H, int64_t W, int64_t pitch, int conn,
               int op, int mode, int64_t steps, int64_t *steps_out, void *stream, int batch);
 int launch_plan(int dt, const TileLaunch &L, int op, int conn, cudaStream_t s, const Plan &P);
+// The same driver for any element type including the internal GEO_D32 (no
+// check of dt against the public geo_dtype values).
+int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64_t H, int64_t W, int64_t pitch,
+                  int conn, int op, int mode, int64_t steps, int64_t *steps_out, void *stream, int batch);
+// Cached plan of the register-resident kernel for an element type, op, item
+// code (0..5 as geo_item.op, for the tune cache) and chain length hint.
+int plan_rr(int dt, int op, int code, int conn, int64_t H, int64_t W, int64_t steps_hint, Plan *P);
 
 // Host-side launcher per element type (defined in geo_tile_<dtype>.cu).
 
@@ -110,6 +121,8 @@ int launch_rr_f64(const TileLaunch &L, int op, int conn, cudaStream_t s, int gri
 int occupancy_rr_u8(int op, int conn, int *blocks_per_sm);
 int occupancy_rr_f32(int op, int conn, int *blocks_per_sm);
 int occupancy_rr_f64(int op, int conn, int *blocks_per_sm);
+int launch_rr_d32(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid);
+int occupancy_rr_d32(int op, int conn, int *blocks_per_sm);
 int occupancy_tile_u8(int op, int conn, size_t smem, int *blocks_per_sm);
 int occupancy_tile_f32(int op, int conn, size_t smem, int *blocks_per_sm);
 int occupancy_tile_f64(int op, int conn, size_t smem, int *blocks_per_sm);

@@ -45,6 +45,8 @@ struct RU8 {
   __device__ static Wd e2(Wd a, Wd b) { return OP == DILATE ? umax2(a, b) : umin2(a, b); }
   __device__ static Wd ext3(Wd a, Wd b, Wd c) { return e2(e2(a, b), c); }
   __device__ static Wd clamp(Wd v, Wd m) { return OP == DILATE ? umin2(v, m) : umax2(v, m); }
+  // new value of a word from its neighbourhood extreme v, mask m and old value
+  __device__ static Wd apply(Wd v, Wd m, Wd) { return clamp(v, m); }
   __device__ static Px ident() { return OP == DILATE ? 0u : 255u; }
   __device__ static Px anti() { return OP == DILATE ? 255u : 0u; }
   __device__ static Wd identw() { return ident() * 0x00010001u; }
@@ -103,6 +105,7 @@ struct RF32 {
   __device__ static Wd e2(Wd a, Wd b) { return OP == DILATE ? fmaxf(a, b) : fminf(a, b); }
   __device__ static Wd ext3(Wd a, Wd b, Wd c) { return OP == DILATE ? fmax3(a, b, c) : fmin3(a, b, c); }
   __device__ static Wd clamp(Wd v, Wd m) { return OP == DILATE ? fminf(v, m) : fmaxf(v, m); }
+  __device__ static Wd apply(Wd v, Wd m, Wd) { return clamp(v, m); }
   __device__ static Px ident() { return OP == DILATE ? -__int_as_float(0x7f800000) : __int_as_float(0x7f800000); }
   __device__ static Px anti() { return OP == DILATE ? __int_as_float(0x7f800000) : -__int_as_float(0x7f800000); }
   __device__ static Wd identw() { return ident(); }
@@ -157,6 +160,7 @@ struct RF64 {
   __device__ static Wd e2(Wd a, Wd b) { return OP == DILATE ? max(a, b) : min(a, b); }
   __device__ static Wd ext3(Wd a, Wd b, Wd c) { return e2(e2(a, b), c); }
   __device__ static Wd clamp(Wd v, Wd m) { return OP == DILATE ? min(v, m) : max(v, m); }
+  __device__ static Wd apply(Wd v, Wd m, Wd) { return clamp(v, m); }
   __device__ static Px ident() { return OP == DILATE ? (long long)0x8000000000000000ULL : 0x7fffffffffffffffLL; }
   __device__ static Px anti() { return OP == DILATE ? 0x7fffffffffffffffLL : (long long)0x8000000000000000ULL; }
   __device__ static Wd identw() { return ident(); }
@@ -242,6 +246,13 @@ template <int OP> using SF64 = RF64<OP, GEO_RR_F64_RW, GEO_RR_F64_NW>;
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
+
+// Observer of the step's writes: called with (word row, column, old, new)
+// for every word a step writes. The plain chains observe nothing.
+struct NoObs {
+  template <class Wd>
+  __device__ __forceinline__ void operator()(int, int, Wd, Wd) const {}
+};
 
 template <class P>
 struct RR {
@@ -340,6 +351,14 @@ struct RR {
   template <int CONN>
   __device__ static bool step(Wd (&w)[RW][CW], const Wd (&m)[RW][CW], Wd *xb, uint64_t *bar, uint32_t parity,
                               int lane, int warp) {
+    NoObs none;
+    return step<CONN>(w, m, xb, bar, parity, lane, warp, none);
+  }
+
+  // the same with an observer of the written words
+  template <int CONN, class Obs>
+  __device__ static bool step(Wd (&w)[RW][CW], const Wd (&m)[RW][CW], Wd *xb, uint64_t *bar, uint32_t parity,
+                              int lane, int warp, Obs &obs) {
     static_assert(RW >= 2, "a band needs distinct first and last word rows");
     Wd *mine = xb + (size_t)(warp + 1) * 2 * RWID + lane * CW;
     const Wd *up_slot = xb + (size_t)warp * 2 * RWID + RWID + lane * CW;
@@ -362,7 +381,11 @@ struct RR {
 #pragma unroll
       for (int r = 1; r < RW - 1; ++r)
 #pragma unroll
-        for (int c = 0; c < CW; ++c) w[r][c] = P::clamp(P::ext3(h[r - 1][c], h[r][c], h[r + 1][c]), m[r][c]);
+        for (int c = 0; c < CW; ++c) {
+          const Wd nv = P::apply(P::ext3(h[r - 1][c], h[r][c], h[r + 1][c]), m[r][c], w[r][c]);
+          obs(r, c, w[r][c], nv);
+          w[r][c] = nv;
+        }
       const bool ok = mbar_wait(bar, parity);
       Wd ha[CW], hb[CW];
       P::unpack(*reinterpret_cast<const uint4 *>(up_slot), ha);
@@ -372,8 +395,12 @@ struct RR {
         // row 3-extremes of the rows just above / below the band halves
         const Wd hu = P::up(ha[c], h[RW - 1][c]);
         const Wd hd = P::down(h[0][c], hb[c]);
-        w[0][c] = P::clamp(P::e2(pre0[c], hu), m[0][c]);
-        w[RW - 1][c] = P::clamp(P::e2(preL[c], hd), m[RW - 1][c]);
+        const Wd n0 = P::apply(P::e2(pre0[c], hu), m[0][c], w[0][c]);
+        const Wd nL = P::apply(P::e2(preL[c], hd), m[RW - 1][c], w[RW - 1][c]);
+        obs(0, c, w[0][c], n0);
+        obs(RW - 1, c, w[RW - 1][c], nL);
+        w[0][c] = n0;
+        w[RW - 1][c] = nL;
       }
       return ok;
     } else {
@@ -398,7 +425,9 @@ struct RR {
 #pragma unroll
         for (int c = 0; c < CW; ++c) {
           const Wd old = w[r][c];
-          w[r][c] = P::clamp(P::ext3(fp[c], h[r][c], w[r + 1][c]), m[r][c]);
+          const Wd nv = P::apply(P::ext3(fp[c], h[r][c], w[r + 1][c]), m[r][c], old);
+          obs(r, c, old, nv);
+          w[r][c] = nv;
           fp[c] = old;
         }
       }
@@ -408,8 +437,12 @@ struct RR {
       P::unpack(*reinterpret_cast<const uint4 *>(dn_slot), below);
 #pragma unroll
       for (int c = 0; c < CW; ++c) {
-        w[0][c] = P::clamp(P::e2(pre0[c], P::up(above[c], last[c])), m[0][c]);
-        w[RW - 1][c] = P::clamp(P::e2(preL[c], P::down(first[c], below[c])), m[RW - 1][c]);
+        const Wd n0 = P::apply(P::e2(pre0[c], P::up(above[c], last[c])), m[0][c], first[c]);
+        const Wd nL = P::apply(P::e2(preL[c], P::down(first[c], below[c])), m[RW - 1][c], last[c]);
+        obs(0, c, first[c], n0);
+        obs(RW - 1, c, last[c], nL);
+        w[0][c] = n0;
+        w[RW - 1][c] = nL;
       }
       return ok;
     }
