@@ -80,6 +80,11 @@ def _load():
             lib.oracle_qdt_residual.restype = I
             lib.oracle_qdt_lipschitz.argtypes = [P, P, L, L, I, L]
             lib.oracle_qdt_lipschitz.restype = L
+            for name in ("oracle_opening", "oracle_closing", "oracle_asf"):
+                getattr(lib, name).argtypes = [P, P, L, L, L]
+                getattr(lib, name).restype = I
+            lib.oracle_granulometry.argtypes = [P, L, L, L, P]
+            lib.oracle_granulometry.restype = I
             _lib = lib
     return _lib
 
@@ -93,7 +98,8 @@ def use_library(path):
     lib = ctypes.CDLL(path)
     for name in ("oracle_step", "oracle_chain", "oracle_reconstruct", "oracle_window",
                  "oracle_chain_backward", "oracle_hmax", "oracle_dome", "oracle_hfill", "oracle_raobj",
-                 "oracle_open_rec", "oracle_qdt_residual", "oracle_qdt_lipschitz"):
+                 "oracle_open_rec", "oracle_qdt_residual", "oracle_qdt_lipschitz", "oracle_opening",
+                 "oracle_closing", "oracle_granulometry", "oracle_asf"):
         fn, ref = getattr(lib, name), getattr(prev, name)
         fn.argtypes, fn.restype = ref.argtypes, ref.restype
     with _lock:
@@ -294,3 +300,44 @@ def qdt(f, conn=8):
     r, d = qdt_residual(f, conn)
     dl1, _ = qdt_lipschitz(d, conn)
     return r, d, dl1
+
+
+# ---------------------------------------------------------------------------
+# granulometry and alternating sequential filters (Section 2, Eq. 16-20)
+# ---------------------------------------------------------------------------
+
+def _win_call(name, f, s):
+    lib = _load()
+    f64 = _f64(f)
+    out = np.empty_like(f64)
+    H, W = f64.shape
+    if getattr(lib, name)(_ptr(f64), _ptr(out), H, W, int(s)) != 0:
+        raise MemoryError(name)
+    return _back(out, np.asarray(f))
+
+
+def opening(f, s):
+    """gamma_s(f) = delta_s(eps_s(f)) as 2s elementary 3x3 steps (Eq. 16)."""
+    return _win_call("oracle_opening", f, s)
+
+
+def closing(f, s):
+    """phi_s(f) = eps_s(delta_s(f)) (Eq. 19)."""
+    return _win_call("oracle_closing", f, s)
+
+
+def asf(f, s):
+    """ASF_s(f) = phi_s gamma_s ... phi_1 gamma_1 (f) (Eq. 20)."""
+    return _win_call("oracle_asf", f, s)
+
+
+def granulometry(f, smax):
+    """(G, PS): G_s = sum of gamma_s(f) for s = 0..smax (Eq. 17) and the
+    pattern spectrum PS_s = G_s - G_{s+1} for s = 0..smax-1 (Eq. 18)."""
+    lib = _load()
+    f64 = _f64(f)
+    H, W = f64.shape
+    G = np.empty(int(smax) + 1, np.float64)
+    if lib.oracle_granulometry(_ptr(f64), H, W, int(smax), _ptr(G)) != 0:
+        raise MemoryError("oracle_granulometry")
+    return G, G[:-1] - G[1:]

@@ -17,6 +17,8 @@
  *   Section 2, Eq. 6-12 geodesic operators built on reconstruction
  *   Section 2, Eq. 13-15 quasi-distance transform (residuals of an erosion
  *                       chain as in Algorithm 6, then the eta iteration)
+ *   Section 2, Eq. 16-20 openings, closings, granulometric function, pattern
+ *                       spectrum and alternating sequential filters
  *
  * Every value is held as a double. uint8 and float32 images convert to double
  * exactly, and the forward operators only select among their inputs, so the
@@ -392,4 +394,69 @@ long oracle_qdt_lipschitz(const double *g, double *out, long H, long W, int conn
     free(eps);
     free(tmp);
     return changing;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Granulometry and alternating sequential filters (Section 2, Eq. 16-20)    */
+/* ------------------------------------------------------------------------ */
+
+/* gamma_s(f) = delta_s(eps_s(f)) (Eq. 16): s elementary erosions eps_1, then s
+ * elementary dilations delta_1 (3x3 square, clipped). phi_s(f) =
+ * eps_s(delta_s(f)) (Eq. 19): the same in the other order. first_op is the
+ * operation applied first (ORA_ERODE for the opening). */
+static int ora_open_close(const double *f, double *out, long H, long W, long s, int first_op)
+{
+    long n = H * W;
+    double *tmp = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    if (!tmp) return -1;
+    int second_op = first_op == ORA_ERODE ? ORA_DILATE : ORA_ERODE;
+    int rc = oracle_chain(f, NULL, tmp, H, W, 8, first_op, s);
+    if (rc == 0) rc = oracle_chain(tmp, NULL, out, H, W, 8, second_op, s);
+    free(tmp);
+    return rc;
+}
+
+int oracle_opening(const double *f, double *out, long H, long W, long s)
+{
+    return ora_open_close(f, out, H, W, s, ORA_ERODE);
+}
+
+int oracle_closing(const double *f, double *out, long H, long W, long s)
+{
+    return ora_open_close(f, out, H, W, s, ORA_DILATE);
+}
+
+/* Granulometric function G_s(f) = sum over P of gamma_s(f) (Eq. 17) for
+ * s = 0..smax into G[0..smax] (gamma_0 is f itself), each opening computed
+ * from f, and the pixel sum taken row by row in double. The pattern spectrum
+ * PS_s = G_s - G_{s+1} (Eq. 18) follows from G. */
+int oracle_granulometry(const double *f, long H, long W, long smax, double *G)
+{
+    long n = H * W;
+    double *g = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    if (!g) return -1;
+    for (long s = 0; s <= smax; ++s) {
+        if (ora_open_close(f, g, H, W, s, ORA_ERODE) != 0) { free(g); return -1; }
+        double sum = 0.0;
+        for (long i = 0; i < n; ++i) sum += g[i];
+        G[s] = sum;
+    }
+    free(g);
+    return 0;
+}
+
+/* ASF_s(f) = phi_s(gamma_s(... phi_1(gamma_1(f)))) (Eq. 20): for k = 1..s,
+ * the opening gamma_k and then the closing phi_k. */
+int oracle_asf(const double *f, double *out, long H, long W, long s)
+{
+    long n = H * W;
+    double *tmp = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    if (!tmp) return -1;
+    memcpy(out, f, (size_t)n * sizeof(double));
+    for (long k = 1; k <= s; ++k) {
+        if (ora_open_close(out, tmp, H, W, k, ORA_ERODE) != 0) { free(tmp); return -1; }
+        if (ora_open_close(tmp, out, H, W, k, ORA_DILATE) != 0) { free(tmp); return -1; }
+    }
+    free(tmp);
+    return 0;
 }

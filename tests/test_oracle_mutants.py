@@ -11,6 +11,7 @@ import oracle
 from tests import test_oracle_ops_pins as ops_pins
 from tests import test_oracle_pins as pins
 from tests import test_oracle_qdt_pins as qdt_pins
+from tests import test_oracle_gran_pins as gran_pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
 
@@ -57,6 +58,18 @@ MUTANTS = [
      "tmp[i] = (out[i] - eps[i] > 1.0) ? eps[i] : out[i];"),
     ("eta_threshold_two", "tmp[i] = (out[i] - eps[i] > 1.0) ? eps[i] + 1.0 : out[i];",
      "tmp[i] = (out[i] - eps[i] > 2.0) ? eps[i] + 1.0 : out[i];"),
+    ("opening_dilates_first", "return ora_open_close(f, out, H, W, s, ORA_ERODE);\n}\n\nint oracle_closing",
+     "return ora_open_close(f, out, H, W, s, ORA_DILATE);\n}\n\nint oracle_closing"),
+    ("open_close_second_step_short", "if (rc == 0) rc = oracle_chain(tmp, NULL, out, H, W, 8, second_op, s);",
+     "if (rc == 0) rc = oracle_chain(tmp, NULL, out, H, W, 8, second_op, s > 1 ? s - 1 : s);"),
+    ("granulometry_previous_size", "if (ora_open_close(f, g, H, W, s, ORA_ERODE) != 0) { free(g); return -1; }",
+     "if (ora_open_close(f, g, H, W, s > 0 ? s - 1 : 0, ORA_ERODE) != 0) { free(g); return -1; }"),
+    ("asf_closing_first", "if (ora_open_close(out, tmp, H, W, k, ORA_ERODE) != 0) { free(tmp); return -1; }\n"
+     "        if (ora_open_close(tmp, out, H, W, k, ORA_DILATE) != 0)",
+     "if (ora_open_close(out, tmp, H, W, k, ORA_DILATE) != 0) { free(tmp); return -1; }\n"
+     "        if (ora_open_close(tmp, out, H, W, k, ORA_ERODE) != 0)"),
+    ("asf_skips_last_level", "for (long k = 1; k <= s; ++k) {\n        if (ora_open_close(out",
+     "for (long k = 1; k < s; ++k) {\n        if (ora_open_close(out"),
 ]
 
 PIN_TESTS = [
@@ -80,6 +93,9 @@ PIN_TESTS = [
     lambda: qdt_pins.test_binary_qdt_is_the_distance_transform(8),
     lambda: qdt_pins.test_grey_residuals_match_minimum_filters(4),
     lambda: qdt_pins.test_lipschitz_limit_closed_form(8),
+    lambda: gran_pins.test_opening_and_closing_match_scipy(),
+    lambda: gran_pins.test_asf_matches_scipy_composition(),
+    lambda: gran_pins.test_granulometry_of_separated_squares(),
 ]
 
 
