@@ -320,7 +320,9 @@ def secondary(dev):
     # geodesic operators of the paper's Table 5 on the 1024^2 u8 workload-1 image
     g = torch.from_numpy(synth.workload1_u8()["mask"]).to(dev)
     ops = {"hmax_h20": lambda: gm.hmax(g, 20), "dome_h20": lambda: gm.dome(g, 20), "hfill": lambda: gm.hfill(g),
-           "raobj": lambda: gm.raobj(g), "open_rec_s15": lambda: gm.open_rec(g, 15)}
+           "raobj": lambda: gm.raobj(g), "open_rec_s15": lambda: gm.open_rec(g, 15),
+           "qdt": lambda: gm.qdt(g), "pattern_spectrum_0_11": lambda: gm.granulometry(g, 11),
+           "asf_11": lambda: gm.asf(g, 11)}
     res["operators_1024_u8"] = {"workload": "1024x1024 u8 workload-1 image, 8-connected",
                                 **{k: {"ms": _time(fn, 3) * 1e3} for k, fn in ops.items()}}
     res["reconstruct_4096"] = {

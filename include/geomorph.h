@@ -185,6 +185,35 @@ GEO_API int geo_qdt(geo_dtype dtype, const void *f, void *r, int32_t *d, int32_t
                     int64_t width, int64_t pitch, int conn, void *stream);
 
 /*
+ * Openings, closings, granulometry and alternating sequential filters
+ * (Section 2, Eq. 16-20), all with the 3x3 square (the paper's w_1) clipped
+ * to the image, eps_s / delta_s being s chained elementary steps:
+ *
+ * geo_opening       gamma_s(f) = delta_s(eps_s(f))                  (Eq. 16)
+ * geo_closing       phi_s(f)   = eps_s(delta_s(f))                  (Eq. 19)
+ * geo_asf           ASF_s(f) = phi_s(gamma_s(... phi_1(gamma_1(f))))  (Eq. 20)
+ * geo_granulometry  G_k = sum over the image of gamma_k(f) for k = 0..smax
+ *                   (Eq. 17) and PS_k = G_k - G_{k+1} for k = 0..smax-1
+ *                   (Eq. 18)
+ *
+ * f, out: device images of `dtype`, H rows of `pitch` elements; out may
+ * equal f (in place) but must not otherwise overlap it. half_size / s >= 0
+ * (0: out = f). G: device double[smax + 1]; PS: device double[smax] or NULL;
+ * both 8-byte aligned. G sums in double with a fixed order: exact for
+ * uint8, deterministic for floats. Errors: GEO_ERR_DTYPE, GEO_ERR_ARG
+ * (negative sizes, pitch < width, NULL pointers, overlap), GEO_ERR_ALIGN.
+ * Asynchronous on stream; scratch comes from the library's pool.
+ */
+GEO_API int geo_opening(geo_dtype dtype, const void *f, void *out, int64_t height, int64_t width, int64_t pitch,
+                        int64_t half_size, void *stream);
+GEO_API int geo_closing(geo_dtype dtype, const void *f, void *out, int64_t height, int64_t width, int64_t pitch,
+                        int64_t half_size, void *stream);
+GEO_API int geo_asf(geo_dtype dtype, const void *f, void *out, int64_t height, int64_t width, int64_t pitch,
+                    int64_t s, void *stream);
+GEO_API int geo_granulometry(geo_dtype dtype, const void *f, int64_t height, int64_t width, int64_t pitch,
+                             int64_t smax, double *G, double *PS, void *stream);
+
+/*
  * Batched execution: many independent items in one persistent launch.
  * The paper has no batched form; item i computes exactly what the matching
  * single-item entry point computes on its own images.

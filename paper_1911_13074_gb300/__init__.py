@@ -122,6 +122,11 @@ def load():
         lib.geo_open_rec.restype = I
         lib.geo_qdt.argtypes = [I, P, P, P, P, L, L, L, I, P]
         lib.geo_qdt.restype = I
+        for name in ("geo_opening", "geo_closing", "geo_asf"):
+            getattr(lib, name).argtypes = [I, P, P, L, L, L, L, P]
+            getattr(lib, name).restype = I
+        lib.geo_granulometry.argtypes = [I, P, L, L, L, L, P, P, P]
+        lib.geo_granulometry.restype = I
         IPtr = ctypes.POINTER(I)
         lib.geo_plan_info.argtypes = [I, I, I, L, L, L, IPtr, IPtr, IPtr]
         lib.geo_plan_info.restype = I
@@ -504,3 +509,48 @@ def qdt(f, conn=8, lipschitz=True):
                          dl1.data_ptr() if lipschitz else None, H, W, pitch, int(conn), _stream(f))
     _check(rc, "geo_qdt")
     return r, d, dl1
+
+
+# ---------------------------------------------------------------------------
+# openings, closings, granulometry, ASF (Section 2, Eq. 16-20)
+# ---------------------------------------------------------------------------
+
+def _win(name, f, s, out):
+    lib = load()
+    _image(f, "f")
+    out = _out_like(f, out)
+    H, W = f.shape
+    with torch.cuda.device(f.device):
+        rc = getattr(lib, name)(DTYPES[f.dtype], f.data_ptr(), out.data_ptr(), H, W, _pitch(f), int(s), _stream(f))
+    _check(rc, name)
+    return out
+
+
+def opening(f, half_size, out=None):
+    """gamma_s(f) = delta_s(eps_s(f)) with the clipped (2s+1)^2 square (Eq. 16)."""
+    return _win("geo_opening", f, half_size, out)
+
+
+def closing(f, half_size, out=None):
+    """phi_s(f) = eps_s(delta_s(f)) (Eq. 19)."""
+    return _win("geo_closing", f, half_size, out)
+
+
+def asf(f, s, out=None):
+    """Alternating sequential filter ASF_s(f) = phi_s gamma_s ... phi_1 gamma_1 (f) (Eq. 20)."""
+    return _win("geo_asf", f, s, out)
+
+
+def granulometry(f, smax):
+    """(G, PS) as float64 CUDA tensors: G_k = sum of gamma_k(f), k = 0..smax
+    (Eq. 17), and the pattern spectrum PS_k = G_k - G_{k+1} (Eq. 18)."""
+    lib = load()
+    _image(f, "f")
+    H, W = f.shape
+    G = torch.empty(int(smax) + 1, dtype=torch.float64, device=f.device)
+    PS = torch.empty(max(int(smax), 1), dtype=torch.float64, device=f.device)
+    with torch.cuda.device(f.device):
+        rc = lib.geo_granulometry(DTYPES[f.dtype], f.data_ptr(), H, W, _pitch(f), int(smax), G.data_ptr(),
+                                  PS.data_ptr(), _stream(f))
+    _check(rc, "geo_granulometry")
+    return G, PS[:int(smax)]
