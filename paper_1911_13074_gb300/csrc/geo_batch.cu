@@ -98,8 +98,8 @@ __device__ bool run_tile(const BItem &it, int tile, int p, int S, typename P::Wd
   const int64_t gy0 = ty0 - it.K + warp * PH;
   const int64_t gx = tx0 - it.K + lane * CW;
   Wd w[RW][CW], m[RW][CW];
-  R::load_words(src, it.H, it.W, gy0, gx, src_cg, false, w);
-  R::load_words(it.mask, it.H, it.W, gy0, gx, false, it.mask.ptr == nullptr, m);
+  R::template load_words<false>(src, it.H, it.W, gy0, gx, src_cg, false, w);
+  R::template load_words<false>(it.mask, it.H, it.W, gy0, gx, false, it.mask.ptr == nullptr, m);
   bool ok = true;
   for (int j = 0; j < S; ++j) {
     ok &= R::template step<CONN>(w, m, xb + (size_t)parity * (kBatchNW + 2) * 2 * R::RWID, bars, parity, lane, warp);

@@ -289,21 +289,85 @@ struct RR {
     }
   }
 
+  // EDGES: also batch the loads of strips that reach past the top / bottom
+  // image border or lie outside it (the single-image kernel; the batch
+  // kernel, which holds every element policy at once, keeps the lighter form
+  // that batches only strips wholly inside the image)
+  template <bool EDGES = true>
   __device__ static void load_words(const Plane &Q, int64_t H, int64_t W, int64_t gy0, int64_t gx, bool cg,
                                     bool virt, Wd (&w)[RW][CW]) {
-    if (!virt && Q.vec_ok && gy0 >= 0 && gy0 + B * RW <= H && gx >= 0 && gx + CW <= W) {
-      // the lane's strip lies inside the image: issue every row's load
-      // before using any, so they are in flight together
+    const bool cols_in = gx >= 0 && gx + CW <= W, cols_out = gx + CW <= 0 || gx >= W;
+    if (!EDGES && !virt && Q.vec_ok && cols_in && gy0 >= 0 && gy0 + B * RW <= H) {
       typename P::Raw raw[B * RW];
-      const char *base = Q.ptr + gy0 * Q.pitch_b + gx * GS;
 #pragma unroll
-      for (int i = 0; i < B * RW; ++i) raw[i] = P::load_raw(base + i * Q.pitch_b, cg);
+      for (int i = 0; i < B * RW; ++i) raw[i] = P::load_raw(Q.ptr + (gy0 + i) * Q.pitch_b + gx * GS, cg);
 #pragma unroll
       for (int r = 0; r < RW; ++r) {
         Px lo[CW], hi[CW];
         P::unpack_raw(raw[r], lo);
         if constexpr (B == 2) {
           P::unpack_raw(raw[RW + r], hi);
+        } else {
+#pragma unroll
+          for (int c = 0; c < CW; ++c) hi[c] = lo[c];
+        }
+#pragma unroll
+        for (int c = 0; c < CW; ++c) w[r][c] = P::make(lo[c], hi[c]);
+      }
+      return;
+    }
+    if (EDGES && !virt && Q.vec_ok && (cols_in || cols_out)) {
+      // The lane's columns lie wholly inside or wholly outside the image:
+      // issue the loads of every row inside before using any, so they are in
+      // flight together; rows (or strips) outside the image take the identity.
+      if constexpr (B == 1) {
+        // one row per word: rows in chunks, which bounds the 16-byte raw
+        // values live at once (f32 / f64 hold 8 rows per lane; f64 words
+        // take two registers each)
+        constexpr int CH = sizeof(Wd) == 8 ? 1 : 4;
+#pragma unroll
+        for (int r0 = 0; r0 < RW; r0 += CH) {
+          typename P::Raw raw[CH];
+          bool in[CH];
+#pragma unroll
+          for (int i = 0; i < CH; ++i) {
+            const int64_t gy = gy0 + r0 + i;
+            in[i] = r0 + i < RW && cols_in && gy >= 0 && gy < H;
+            if (in[i]) raw[i] = P::load_raw(Q.ptr + gy * Q.pitch_b + gx * GS, cg);
+          }
+#pragma unroll
+          for (int i = 0; i < CH; ++i) {
+            if (r0 + i >= RW) break;
+            Px v[CW];
+            P::unpack_raw(raw[i], v);
+#pragma unroll
+            for (int c = 0; c < CW; ++c) w[r0 + i][c] = P::make(in[i] ? v[c] : P::ident(), v[c]);
+          }
+        }
+        return;
+      }
+      typename P::Raw raw[B * RW];
+      bool in[B * RW];
+#pragma unroll
+      for (int i = 0; i < B * RW; ++i) {
+        const int64_t gy = gy0 + i;
+        in[i] = cols_in && gy >= 0 && gy < H;
+        if (in[i]) raw[i] = P::load_raw(Q.ptr + gy * Q.pitch_b + gx * GS, cg);
+      }
+#pragma unroll
+      for (int r = 0; r < RW; ++r) {
+        Px lo[CW], hi[CW];
+        P::unpack_raw(raw[r], lo);
+        if (!in[r]) {
+#pragma unroll
+          for (int c = 0; c < CW; ++c) lo[c] = P::ident();
+        }
+        if constexpr (B == 2) {
+          P::unpack_raw(raw[RW + r], hi);
+          if (!in[RW + r]) {
+#pragma unroll
+            for (int c = 0; c < CW; ++c) hi[c] = P::ident();
+          }
         } else {
 #pragma unroll
           for (int c = 0; c < CW; ++c) hi[c] = lo[c];
