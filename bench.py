@@ -43,6 +43,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-secondary", action="store_true",
                    help="skip the batched and forward+backward comparisons")
+    p.add_argument("--chain-steps", type=int, default=CHAIN_STEPS,
+                   help="chain length of a bench step (default 1500; shorter only for small profiler captures, "
+                        "and then named in the output's config)")
     return p.parse_args()
 
 
@@ -120,13 +123,17 @@ def measured_peaks():
         return {}
 
 
+# the sources that define the timed chain kernel (rr_kernel for uint8) and its launch
+CHAIN_KERNEL_SOURCES = ("geo_common.cuh", "geo_tile.cuh", "geo_rr.cuh", "geo_launch.cuh", "geo_tile_u8.cu",
+                        "geo_api.cu")
+
+
 def kernel_source_sha256():
-    import glob
     import hashlib
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1911_13074_gb300", "csrc", "*.cu*"))):
-        h.update(os.path.basename(p).encode())
-        with open(p, "rb") as fh:
+    for name in CHAIN_KERNEL_SOURCES:
+        h.update(name.encode())
+        with open(os.path.join(ROOT, "paper_1911_13074_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
@@ -364,7 +371,7 @@ def main():
         torch.cuda.synchronize(dev)
 
     for _ in range(args.warmup):
-        gm.dilate_chain(marker, mask, CHAIN_STEPS, conn=CONN, out=out)
+        gm.dilate_chain(marker, mask, args.chain_steps, conn=CONN, out=out)
     torch.cuda.synchronize(dev)
     if gm.device_status() != 0:
         raise RuntimeError("device status error during warm-up")
@@ -379,7 +386,7 @@ def main():
     for i in range(args.steps):
         flush.fill_(i & 0xFF)
         ev[i][0].record(stream)
-        gm.dilate_chain(marker, mask, CHAIN_STEPS, conn=CONN, out=out)
+        gm.dilate_chain(marker, mask, args.chain_steps, conn=CONN, out=out)
         ev[i][1].record(stream)
     barrier()
     t_wall = time.perf_counter() - t_wall
@@ -399,7 +406,7 @@ def main():
     for _ in range(args.steps):
         mk = marker_h.to(dev, non_blocking=True)
         ms = mask_h.to(dev, non_blocking=True)
-        gm.dilate_chain(mk, ms, CHAIN_STEPS, conn=CONN, out=out)
+        gm.dilate_chain(mk, ms, args.chain_steps, conn=CONN, out=out)
         out_h.copy_(out, non_blocking=True)
     e1.record(stream)
     barrier()
@@ -412,7 +419,7 @@ def main():
             dist.destroy_process_group()
         return
 
-    px_steps = H * W * CHAIN_STEPS
+    px_steps = H * W * args.chain_steps
     value = whole_job_rate(world, px_steps, args.steps, t_dev)
     e2e_value = whole_job_rate(world, px_steps, args.steps, t_e2e)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -425,7 +432,9 @@ def main():
         "metric": METRIC, "value": value, "unit": "Gpixel-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "H": H, "W": W, "chain_steps": CHAIN_STEPS, "conn": CONN,
+        "config": {"workload": WORKLOAD if args.chain_steps == CHAIN_STEPS else
+                   WORKLOAD.replace(f"{CHAIN_STEPS} steps", f"{args.chain_steps} steps (shortened)"),
+                   "H": H, "W": W, "chain_steps": args.chain_steps, "conn": CONN,
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "flushed between timed chains (256 MiB write, outside the events)"},
         "fps": args.steps / t_dev,
