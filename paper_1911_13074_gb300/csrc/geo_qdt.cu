@@ -35,6 +35,7 @@ struct RD32 {
   static constexpr uint32_t kIdent = 0x7fffu;  // above every distance, and +1 stays inside the lane
   __device__ static Wd e2(Wd a, Wd b) { return umin2(a, b); }
   __device__ static Wd ext3(Wd a, Wd b, Wd c) { return umin2(umin2(a, b), c); }
+  __device__ static Wd ext3h(Wd a, Wd b, Wd c) { return ext3(a, b, c); }
   __device__ static Wd clamp(Wd v, Wd m) { return umax2(v, m); }
   // eta on both lanes: min(old, eps_1 + 1), then the virtual mask keeps the
   // cells outside the image at the identity

@@ -36,15 +36,44 @@ namespace geo {
 // register-resident element policies
 // ---------------------------------------------------------------------------
 
+// Bit mask of the u8 step's min/max groups issued as f16x2 instead of
+// u16x2 (1: row extremes, 2: column extremes, 4: mask clamp). The u8 values
+// 0..255 in u16 lanes are, read as f16, +0 and positive subnormals whose
+// order is the integer order (no flush to zero, no NaN, no -0), so both
+// forms select the same lane values; on the 1024^2 1500-step chain the f16
+// form measured about 3 % faster (0.78 vs 0.80 ms), whichever group uses it.
+#ifndef GEO_RR_U8_F16
+#define GEO_RR_U8_F16 7
+#endif
+__device__ __forceinline__ uint32_t hmax2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("max.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t hmin2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("min.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+
 template <int OP, int RW_ = 4, int NW_ = 16>
 struct RU8 {
   using Wd = uint32_t;  // two u16 lanes: rows r and r + RW of one column
   using Px = uint32_t;  // one pixel value (0..255)
   using G = uint8_t;
   static constexpr int BANDS = 2, CW = 4, RW = RW_, NW = NW_, GS = 1;
-  __device__ static Wd e2(Wd a, Wd b) { return OP == DILATE ? umax2(a, b) : umin2(a, b); }
+  __device__ static Wd e2i(Wd a, Wd b) { return OP == DILATE ? umax2(a, b) : umin2(a, b); }
+  __device__ static Wd e2f(Wd a, Wd b) { return OP == DILATE ? hmax2(a, b) : hmin2(a, b); }
+  __device__ static Wd e2(Wd a, Wd b) { return (GEO_RR_U8_F16 & 2) ? e2f(a, b) : e2i(a, b); }
   __device__ static Wd ext3(Wd a, Wd b, Wd c) { return e2(e2(a, b), c); }
-  __device__ static Wd clamp(Wd v, Wd m) { return OP == DILATE ? umin2(v, m) : umax2(v, m); }
+  // the row 3-extreme (hrow)
+  __device__ static Wd ext3h(Wd a, Wd b, Wd c) {
+    return (GEO_RR_U8_F16 & 1) ? e2f(e2f(a, b), c) : e2i(e2i(a, b), c);
+  }
+  __device__ static Wd clamp(Wd v, Wd m) {
+    if (GEO_RR_U8_F16 & 4) return OP == DILATE ? hmin2(v, m) : hmax2(v, m);
+    return OP == DILATE ? umin2(v, m) : umax2(v, m);
+  }
   // new value of a word from its neighbourhood extreme v, mask m and old value
   __device__ static Wd apply(Wd v, Wd m, Wd) { return clamp(v, m); }
   __device__ static Px ident() { return OP == DILATE ? 0u : 255u; }
@@ -104,6 +133,7 @@ struct RF32 {
   static constexpr int BANDS = 1, CW = 4, RW = RW_, NW = NW_, GS = 4;
   __device__ static Wd e2(Wd a, Wd b) { return OP == DILATE ? fmaxf(a, b) : fminf(a, b); }
   __device__ static Wd ext3(Wd a, Wd b, Wd c) { return OP == DILATE ? fmax3(a, b, c) : fmin3(a, b, c); }
+  __device__ static Wd ext3h(Wd a, Wd b, Wd c) { return ext3(a, b, c); }
   __device__ static Wd clamp(Wd v, Wd m) { return OP == DILATE ? fminf(v, m) : fmaxf(v, m); }
   __device__ static Wd apply(Wd v, Wd m, Wd) { return clamp(v, m); }
   __device__ static Px ident() { return OP == DILATE ? -__int_as_float(0x7f800000) : __int_as_float(0x7f800000); }
@@ -159,6 +189,7 @@ struct RF64 {
   static constexpr int BANDS = 1, CW = 2, RW = RW_, NW = NW_, GS = 8;
   __device__ static Wd e2(Wd a, Wd b) { return OP == DILATE ? max(a, b) : min(a, b); }
   __device__ static Wd ext3(Wd a, Wd b, Wd c) { return e2(e2(a, b), c); }
+  __device__ static Wd ext3h(Wd a, Wd b, Wd c) { return ext3(a, b, c); }
   __device__ static Wd clamp(Wd v, Wd m) { return OP == DILATE ? min(v, m) : max(v, m); }
   __device__ static Wd apply(Wd v, Wd m, Wd) { return clamp(v, m); }
   __device__ static Px ident() { return OP == DILATE ? (long long)0x8000000000000000ULL : 0x7fffffffffffffffLL; }
@@ -396,10 +427,10 @@ struct RR {
   __device__ static void hrow(const Wd (&row)[CW], Wd (&h)[CW]) {
     const Wd left = __shfl_up_sync(0xffffffffu, row[CW - 1], 1);
     const Wd right = __shfl_down_sync(0xffffffffu, row[0], 1);
-    h[0] = P::ext3(left, row[0], row[1]);
+    h[0] = P::ext3h(left, row[0], row[1]);
 #pragma unroll
-    for (int c = 1; c < CW - 1; ++c) h[c] = P::ext3(row[c - 1], row[c], row[c + 1]);
-    h[CW - 1] = P::ext3(row[CW - 2], row[CW - 1], right);
+    for (int c = 1; c < CW - 1; ++c) h[c] = P::ext3h(row[c - 1], row[c], row[c + 1]);
+    h[CW - 1] = P::ext3h(row[CW - 2], row[CW - 1], right);
   }
 
   // One elementary step, in place, on the lane's words. The band's boundary
