@@ -61,34 +61,66 @@ struct SegGeom {
   static constexpr size_t smem = 3 * f_bytes + code_bytes + 2 * g_bytes;
 };
 
-// One forward cell: neighbourhood extreme (lowest index on ties), mask branch.
-// `checked`: clip the neighbourhood to the image (tiles near the border).
-template <typename T, int OP, int CONN, int RF, bool checked>
-__device__ __forceinline__ void seg_cell(const T *cur, const T *ms, int r, int c, int y, int x, int H, int W, T &out,
-                                         uint8_t &code) {
-  T best = T(0);
-  int bk = -1;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    if (!in_shape<CONN>(k)) continue;
-    const int dy = k / 3 - 1, dx = k % 3 - 1;
-    if (checked && (y + dy < 0 || y + dy >= H || x + dx < 0 || x + dx >= W)) continue;
-    const T v = cur[(r + dy) * RF + (c + dx)];
-    if (bk < 0 || (OP == DILATE ? (v > best) : (v < best))) {
-      best = v;
-      bk = k;
-    }
-  }
-  const T mv = ms[r * RF + c];
-  const bool to_mask = (OP == DILATE) ? (mv < best) : (mv > best);
-  out = to_mask ? mv : best;
-  code = to_mask ? kRouteMask : (uint8_t)bk;
+// Identity of the neighbourhood extreme: what cells outside the image hold
+// (image and mask) in the shared-memory regions, so that they never win an
+// extreme, stay at the identity step after step (the mask clamp keeps them
+// there) and never receive a gradient.
+template <typename T, int OP>
+__device__ __forceinline__ T seg_ident() {
+  if (sizeof(T) == 4) return (T)(OP == DILATE ? __int_as_float(0xff800000) : __int_as_float(0x7f800000));
+  return (T)(OP == DILATE ? __longlong_as_double((long long)0xfff0000000000000ULL)
+                          : __longlong_as_double(0x7ff0000000000000LL));
 }
+
+template <typename T, int OP>
+__device__ __forceinline__ bool beats(T v, T best) {
+  return OP == DILATE ? (v > best) : (v < best);
+}
+
+// Row extreme of one row at columns c-1, c, c+1 with the lowest dx on ties
+// (a = 0, 1, 2), and the centre value (the cross uses only the centre of
+// the rows above and below).
+template <typename T, int OP>
+struct RowExt {
+  T m, ctr;
+  int a;
+  __device__ __forceinline__ void load(const T *row, int c) {
+    const T v0 = row[c - 1], v1 = row[c], v2 = row[c + 1];
+    m = v0;
+    a = 0;
+    if (beats<T, OP>(v1, m)) {
+      m = v1;
+      a = 1;
+    }
+    if (beats<T, OP>(v2, m)) {
+      m = v2;
+      a = 2;
+    }
+    ctr = v1;
+  }
+};
+
+// The threads of a CTA as (column, chunk of rows) of a region of side R:
+// thread t takes column t % R and rows [chunk * RP, chunk * RP + RP).
+template <int R>
+struct Strips {
+  static constexpr int NH = kSegThreads / R;        // chunks
+  static constexpr int RP = (R + NH - 1) / NH;      // rows per chunk
+};
 
 // f0: the state at the segment start, packed (row stride W). S <= SS steps
 // t0+1 .. t0+S are recomputed; then g at t0+S (g_in) is carried back to t0
 // (g_out) and grad_mask gathers the mask-routed gradients of those steps in
 // decreasing step order (written, not accumulated, when `first`).
+//
+// Forward: every thread walks one column over its chunk of rows with a
+// sliding window of three row extremes, so each row extreme (and its lowest
+// dx) is computed once and used by three cells; the cell's neighbourhood
+// extreme is the first of the rows above / at / below that attains the
+// largest row extreme, which is the lowest index k = (dy+1)*3 + (dx+1) in
+// row-major order. Reverse: the same walk with a window of three rows of
+// routing codes and gradients; each cell adds the gradients routed to it in
+// increasing k.
 template <typename T, int OP, int CONN, int TT, int SS>
 __global__ void __launch_bounds__(kSegThreads) seg_backward(const T *__restrict__ f0, const T *__restrict__ mask,
                                                             int64_t mpitch, const T *__restrict__ g_in,
@@ -97,6 +129,8 @@ __global__ void __launch_bounds__(kSegThreads) seg_backward(const T *__restrict_
                                                             int S, int first) {
   using G = SegGeom<T, TT, SS>;
   constexpr int RF = G::RF, RB = G::RB;
+  using SF = Strips<RF>;
+  using SB = Strips<RB>;
   extern __shared__ __align__(16) char smem[];
   T *fa = reinterpret_cast<T *>(smem);
   T *fb = reinterpret_cast<T *>(smem + G::f_bytes);
@@ -104,46 +138,72 @@ __global__ void __launch_bounds__(kSegThreads) seg_backward(const T *__restrict_
   uint8_t *codes = reinterpret_cast<uint8_t *>(smem + 3 * G::f_bytes);
   T *ga = reinterpret_cast<T *>(smem + 3 * G::f_bytes + G::code_bytes);
   T *gb = reinterpret_cast<T *>(smem + 3 * G::f_bytes + G::code_bytes + G::g_bytes);
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kSegT + tx;
   const int b = blockIdx.z;
   const int ty0 = blockIdx.y * TT, tx0 = blockIdx.x * TT;
   const int fy0 = ty0 - 2 * SS, fx0 = tx0 - 2 * SS;  // forward region origin (global)
   const int by0 = ty0 - SS, bx0 = tx0 - SS;          // reverse region origin (global)
-  // the whole forward region inside the image: no clipping needed anywhere
-  const bool inner = fy0 >= 0 && fx0 >= 0 && fy0 + RF <= H && fx0 + RF <= W;
+  const T ID = seg_ident<T, OP>();
   const T *fimg = f0 + (size_t)b * H * W;
   const T *mimg = mask + (size_t)b * H * mpitch;
-  // stage f0 and the mask on the forward region
+  // stage f0 and the mask on the forward region (the identity outside the image)
   for (int r = ty; r < RF; r += kSegT) {
     const int y = fy0 + r;
     for (int c = tx; c < RF; c += kSegT) {
       const int x = fx0 + c;
       const bool in = y >= 0 && y < H && x >= 0 && x < W;
-      fa[r * RF + c] = in ? fimg[(size_t)y * W + x] : T(0);
-      ms[r * RF + c] = in ? mimg[(size_t)y * mpitch + x] : T(0);
+      fa[r * RF + c] = in ? fimg[(size_t)y * W + x] : ID;
+      ms[r * RF + c] = in ? mimg[(size_t)y * mpitch + x] : ID;
     }
   }
   __syncthreads();
   // forward: step j computes the cells within 2SS - j of the tile and keeps
   // the routing codes of the cells within SS of it
+  const int fcol = tid % RF, fchunk = tid / RF;
   T *cur = fa, *nxt = fb;
   for (int j = 1; j <= S; ++j) {
     const int lo = j, hi = RF - j;  // rows / cols [lo, hi) of the forward region
     uint8_t *ct = codes + (size_t)(j - 1) * RB * RB;
-    for (int r = lo + ty; r < hi; r += kSegT) {
-      const int y = fy0 + r;
-      for (int c = lo + tx; c < hi; c += kSegT) {
-        const int x = fx0 + c;
-        uint8_t code = 0xff;  // outside the image: matches no neighbour index
-        T out = T(0);
-        if (inner) {
-          seg_cell<T, OP, CONN, RF, false>(cur, ms, r, c, y, x, H, W, out, code);
-        } else if (y >= 0 && y < H && x >= 0 && x < W) {
-          seg_cell<T, OP, CONN, RF, true>(cur, ms, r, c, y, x, H, W, out, code);
+    const int c = fcol;
+    const int r0 = max(lo, fchunk * SF::RP), r1 = min(hi, fchunk * SF::RP + SF::RP);
+    if (fchunk < SF::NH && c >= lo && c < hi && r0 < r1) {
+      RowExt<T, OP> up, mid, dn;
+      up.load(cur + (r0 - 1) * RF, c);
+      mid.load(cur + r0 * RF, c);
+      for (int r = r0; r < r1; ++r) {
+        dn.load(cur + (r + 1) * RF, c);
+        T best;
+        int k;
+        if (CONN == 8) {
+          best = up.m;
+          k = up.a;
+          if (beats<T, OP>(mid.m, best)) {
+            best = mid.m;
+            k = 3 + mid.a;
+          }
+          if (beats<T, OP>(dn.m, best)) {
+            best = dn.m;
+            k = 6 + dn.a;
+          }
+        } else {  // the cross: k = 1, 3, 4, 5, 7
+          best = up.ctr;
+          k = 1;
+          if (beats<T, OP>(mid.m, best)) {
+            best = mid.m;
+            k = 3 + mid.a;
+          }
+          if (beats<T, OP>(dn.ctr, best)) {
+            best = dn.ctr;
+            k = 7;
+          }
         }
-        nxt[r * RF + c] = out;
+        const T mv = ms[r * RF + c];
+        const bool to_mask = beats<T, OP>(best, mv);  // mask strictly beyond the extreme
+        nxt[r * RF + c] = to_mask ? mv : best;
         const int rb = r - SS, cb = c - SS;
-        if (rb >= 0 && rb < RB && cb >= 0 && cb < RB) ct[rb * RB + cb] = code;
+        if (rb >= 0 && rb < RB && cb >= 0 && cb < RB) ct[rb * RB + cb] = to_mask ? kRouteMask : (uint8_t)k;
+        up = mid;
+        mid = dn;
       }
     }
     __syncthreads();
@@ -173,6 +233,7 @@ __global__ void __launch_bounds__(kSegThreads) seg_backward(const T *__restrict_
       gmacc[e][f] = (!first && r < TT && c < TT && y < H && x < W) ? gmimg[(size_t)y * gm_pitch + x] : T(0);
     }
   __syncthreads();
+  const int bcol = tid % RB, bchunk = tid / RB;
   T *gc = ga, *gn = gb;
   for (int j = S; j >= 1; --j) {
     const uint8_t *ct = codes + (size_t)(j - 1) * RB * RB;
@@ -184,18 +245,48 @@ __global__ void __launch_bounds__(kSegThreads) seg_backward(const T *__restrict_
         const int r = SS + ty + e * kSegT, c = SS + tx + f * kSegT;
         if (ty + e * kSegT < TT && tx + f * kSegT < TT && ct[r * RB + c] == kRouteMask) gmacc[e][f] += gc[r * RB + c];
       }
-    // g at t0 + j - 1 on the cells within j - 1 of the tile
+    // g at t0 + j - 1 on the cells within j - 1 of the tile: cell q gathers
+    // g(p) from p = q - d_k for k = 0..8 where p routed to k; in row terms
+    // k = 0..2 read the row below (columns c+1, c, c-1), k = 3..5 the own
+    // row, k = 6..8 the row above
     const int lo = SS - (j - 1), hi = RB - lo;
-    for (int r = lo + ty; r < hi; r += kSegT) {
-      for (int c = lo + tx; c < hi; c += kSegT) {
+    const int c = bcol;
+    const int r0 = max(lo, bchunk * SB::RP), r1 = min(hi, bchunk * SB::RP + SB::RP);
+    if (bchunk < SB::NH && c >= lo && c < hi && r0 < r1) {
+      // window: codes and gradients of rows r-1 (A), r (B), r+1 (C) at columns c+1, c, c-1
+      uint8_t kA[3], kB[3], kC[3];
+      T gA[3], gB[3], gC[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        kA[i] = ct[(r0 - 1) * RB + c + 1 - i];
+        gA[i] = gc[(r0 - 1) * RB + c + 1 - i];
+        kB[i] = ct[r0 * RB + c + 1 - i];
+        gB[i] = gc[r0 * RB + c + 1 - i];
+      }
+      for (int r = r0; r < r1; ++r) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          kC[i] = ct[(r + 1) * RB + c + 1 - i];
+          gC[i] = gc[(r + 1) * RB + c + 1 - i];
+        }
         T acc = T(0);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-          if (!in_shape<CONN>(k)) continue;
-          const int pr = r - (k / 3 - 1), pc = c - (k % 3 - 1);
-          if (ct[pr * RB + pc] == k) acc += gc[pr * RB + pc];
-        }
+        for (int i = 0; i < 3; ++i)  // k = i: p in the row below
+          if (in_shape<CONN>(i)) acc = kC[i] == i ? acc + gC[i] : acc;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)  // k = 3 + i: the own row
+          if (in_shape<CONN>(3 + i)) acc = kB[i] == 3 + i ? acc + gB[i] : acc;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)  // k = 6 + i: the row above
+          if (in_shape<CONN>(6 + i)) acc = kA[i] == 6 + i ? acc + gA[i] : acc;
         gn[r * RB + c] = acc;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          kA[i] = kB[i];
+          gA[i] = gB[i];
+          kB[i] = kC[i];
+          gB[i] = gC[i];
+        }
       }
     }
     __syncthreads();
