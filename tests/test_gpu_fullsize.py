@@ -123,3 +123,34 @@ def test_workload3_full_batch_equals_single_item_calls():
         ref = (oracle.chain(f, g, it["steps"], conn=it["conn"], op="dilate" if op == 0 else "erode") if op in (0, 1)
                else oracle.reconstruct(f, g, conn=it["conn"], op="dilate" if op == 2 else "erode")[0])
         np.testing.assert_array_equal(b.outs[i].cpu().numpy(), ref)
+
+
+def test_chain_and_window_past_32bit_offsets():
+    """A 48000x48000 uint8 image (2.3e9 pixels, so byte offsets pass 2^31):
+    a 6-step masked dilation chain and a 7x7 window dilation, checked on crops
+    at the corners, the edges and the middle. A crop is computed by the oracle
+    from the crop plus a halo as wide as the step count (or the image border),
+    which fixes the crop exactly."""
+    m = gm()
+    H = W = 48000
+    N, s = 6, 3
+    gen = torch.Generator(device="cuda").manual_seed(0x6E0D00FF)
+    mask = torch.randint(0, 256, (H, W), dtype=torch.uint8, device="cuda", generator=gen)
+    marker = torch.clamp(mask, min=40) - 40  # saturating mask - 40
+    out = m.dilate_chain(marker, mask, N, conn=8)
+    win = m.window_dilate(mask, s)
+    torch.cuda.synchronize()
+    assert m.device_status() == 0
+    C = 64
+    for y0, x0 in [(0, 0), (0, W - C), (H - C, 0), (H - C, W - C), (H // 2 + 3, W // 2 - 5), (H - C, W // 3),
+                   (46341, 46339)]:
+        ya, yb = max(0, y0 - N), min(H, y0 + C + N)
+        xa, xb = max(0, x0 - N), min(W, x0 + C + N)
+        mk = marker[ya:yb, xa:xb].cpu().numpy()
+        ms = mask[ya:yb, xa:xb].cpu().numpy()
+        ref = oracle.chain(mk, ms, N, conn=8)[y0 - ya:y0 - ya + C, x0 - xa:x0 - xa + C]
+        np.testing.assert_array_equal(out[y0:y0 + C, x0:x0 + C].cpu().numpy(), ref, err_msg=f"chain at {y0},{x0}")
+        refw = oracle.window(ms, s)[y0 - ya:y0 - ya + C, x0 - xa:x0 - xa + C]
+        np.testing.assert_array_equal(win[y0:y0 + C, x0:x0 + C].cpu().numpy(), refw, err_msg=f"window at {y0},{x0}")
+    del mask, marker, out, win
+    torch.cuda.empty_cache()
