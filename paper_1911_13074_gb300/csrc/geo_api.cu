@@ -331,8 +331,26 @@ int run_chain(int dt, const void *marker, const void *mask, void *out, int64_t H
   return run_chain_any(dt, marker, mask, out, H, W, pitch, conn, op, mode, steps, steps_out, stream, batch);
 }
 
+// Failure injection on the host (GEOMORPH_FAULT), for testing how failures
+// are reported without faulting a GPU: "badarg" rejects the call as an
+// invalid argument, "alloc" fails the scratch allocation, and "timeout"
+// launches normally but makes every wait on another CTA (neighbour epochs,
+// grid barrier) wait for something that never happens, so that it expires
+// after kFaultWaitNs and the kernel records GEO_ERR_TIMEOUT and returns.
+enum Fault { FAULT_NONE = 0, FAULT_BADARG, FAULT_ALLOC, FAULT_TIMEOUT };
+static Fault injected_fault() {
+  const char *e = getenv("GEOMORPH_FAULT");
+  if (!e) return FAULT_NONE;
+  if (strcmp(e, "badarg") == 0) return FAULT_BADARG;
+  if (strcmp(e, "alloc") == 0) return FAULT_ALLOC;
+  if (strcmp(e, "timeout") == 0) return FAULT_TIMEOUT;
+  return FAULT_NONE;
+}
+
 int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64_t H, int64_t W, int64_t pitch,
                   int conn, int op, int mode, int64_t steps, int64_t *steps_out, void *stream, int batch) {
+  const Fault fault = injected_fault();
+  if (fault == FAULT_BADARG) return GEO_ERR_ARG;
   if (batch < 1) return GEO_ERR_ARG;
   if (H < 0 || W < 0 || pitch < W || (conn != 4 && conn != 8) || (op != DILATE && op != ERODE))
     return GEO_ERR_ARG;
@@ -374,7 +392,8 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
   const size_t ctl_b = 256 + ((3 * ntiles * sizeof(int) + 255) / 256) * 256;
   const size_t scratch_b = ctl_b + (size_t)spitch_b * (size_t)H * (size_t)batch;
   void *scratch = nullptr;
-  if (cudaMallocFromPoolAsync(&scratch, scratch_b, ds->pool, s) != cudaSuccess) return GEO_ERR_CUDA;
+  if (fault == FAULT_ALLOC || cudaMallocFromPoolAsync(&scratch, scratch_b, ds->pool, s) != cudaSuccess)
+    return GEO_ERR_CUDA;
   rc = GEO_OK;
   if (cudaMemsetAsync(scratch, 0, ctl_b, s) != cudaSuccess) rc = GEO_ERR_CUDA;
 
@@ -404,6 +423,8 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
   L.tchg = L.epoch + ntiles;
   L.status = ds->status;
   L.steps_out = steps_out;
+  L.fault = fault == FAULT_TIMEOUT ? 1 : 0;
+  L.wait_ns = L.fault ? kFaultWaitNs : kWaitLimitNs;
   if (mode == MODE_CHAIN) {
     int64_t np = cdiv(steps, P.K);
     if (alias && (np & 1)) ++np;  // pass 0 must not write the buffer it reads

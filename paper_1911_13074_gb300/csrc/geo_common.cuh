@@ -17,6 +17,11 @@ constexpr int GEO_D32 = 3;
 
 constexpr int kThreads = 256;  // threads per CTA of the tile kernels
 
+// A spin on another CTA gives up after this long and records GEO_ERR_TIMEOUT
+// (TileLaunch::wait_ns; GEOMORPH_FAULT=timeout shortens it to kFaultWaitNs).
+constexpr unsigned long long kWaitLimitNs = 4000000000ULL;  // 4 s
+constexpr unsigned long long kFaultWaitNs = 20000000ULL;    // 20 ms
+
 // Band height (word rows per warp) and warps per CTA of the single-image
 // register-resident kernel, per element type.
 #ifndef GEO_RR_U8_RW
@@ -74,6 +79,9 @@ struct TileLaunch {
   int batch;              // images of equal shape, one after another (<= 1: one image)
   int *epoch;             // register kernel, chains: per tile, passes completed
   int *tchg;              // register kernel, reconstruction: [2][tiles] changed flags per pass
+  unsigned long long wait_ns;  // limit of every wait on another CTA
+  int fault;              // injected failure (GEOMORPH_FAULT=timeout): the waits on other CTAs
+                          // wait for something that never happens, expire and report GEO_ERR_TIMEOUT
 };
 
 // Tile geometry of one launch: interior TH x TW, halo K, shared-memory row

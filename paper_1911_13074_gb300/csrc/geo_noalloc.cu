@@ -172,6 +172,7 @@ extern "C" int geo_dilate_chain_noalloc(geo_dtype dtype, const void *marker, con
   L.rs = P.rs;
   L.mode = MODE_CHAIN;
   L.steps = steps;
+  L.wait_ns = kWaitLimitNs;
   int64_t np = (steps + P.K - 1) / P.K;
   if (alias && (np & 1)) ++np;  // pass 0 must not write the buffer it reads
   L.npasses = (int)np;

@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(QP::NW * 32, 1) qdt_kernel(const TileLaunch L,
       const int64_t ty0 = (int64_t)ty * TH, tx0 = (int64_t)tx * TW;
       const int64_t gy0 = ty0 - K + warp * PH, gx = tx0 - K + lane * CW;
       if (pass > 0) {
-        if (warp == 0 && !wait_neighbours(L.epoch, ty, tx, L.tiles_y, L.tiles_x, pass, lane) && lane == 0)
+        if (warp == 0 && !wait_neighbours(L.epoch, ty, tx, L.tiles_y, L.tiles_x, pass, lane, L.wait_ns) && lane == 0)
           record_status(L.status, GEO_ERR_TIMEOUT);
         __syncthreads();
       }
@@ -354,6 +354,7 @@ int geo_qdt(geo_dtype dtype, const void *f, void *r, int32_t *d, int32_t *d_l1, 
   L.epoch = (int *)((char *)scratch + 256);
   L.status = status;
   L.batch = 1;
+  L.wait_ns = kWaitLimitNs;
   const Plane Rp = plane(r, pitch, QP::CW), Dp = plane(d, pitch * 4, QP::CW * 4);
   if (rc == GEO_OK) {
     void *k = conn == 8 ? qdt_kernel_ptr<8>() : qdt_kernel_ptr<4>();

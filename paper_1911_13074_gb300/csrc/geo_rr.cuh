@@ -590,7 +590,7 @@ struct RR {
 // neighbour k, so the eight acquire loads are in flight together instead of
 // one after another. Bounded; false (on every lane) if a wait expired.
 __device__ __forceinline__ bool wait_neighbours(const int *epoch, int ty, int tx, int tiles_y, int tiles_x,
-                                                int want, int lane) {
+                                                int want, int lane, unsigned long long limit_ns) {
   bool ok = true;
   if (lane < 9 && lane != 4) {
     const int ny = ty + lane / 3 - 1, nx = tx + lane % 3 - 1;
@@ -599,7 +599,7 @@ __device__ __forceinline__ bool wait_neighbours(const int *epoch, int ty, int tx
       const unsigned long long t0 = globaltimer_ns();
       unsigned spins = 0;
       while ((int)ld_acquire_u32(f) < want) {
-        if ((++spins & 255u) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) {
+        if ((++spins & 255u) == 0 && globaltimer_ns() - t0 > limit_ns) {
           ok = false;
           break;
         }
@@ -691,7 +691,8 @@ __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
         // tile's halo reads must have finished the previous pass (which also
         // means they are done reading the buffer this pass overwrites)
         if (warp == 0 &&
-            !wait_neighbours(L.epoch + (size_t)bi * tiles_img, ty, tx, L.tiles_y, L.tiles_x, pass, lane) &&
+            !wait_neighbours(L.epoch + (size_t)bi * tiles_img, ty, tx, L.tiles_y, L.tiles_x,
+                             L.fault ? pass + (1 << 28) : pass, lane, L.wait_ns) &&
             lane == 0)
           record_status(L.status, GEO_ERR_TIMEOUT);
         __syncthreads();
@@ -749,7 +750,7 @@ __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
       if (pass == L.npasses - 1) break;
       continue;  // no grid barrier between chain passes (every wait is bounded)
     }
-    if (!grid_barrier(L.ctl, L.status, gridDim.x)) return;
+    if (!grid_barrier(L.ctl, L.status, gridDim.x + (L.fault ? 1u : 0u), L.wait_ns)) return;
     if (rec) {
       const int f = *(volatile int *)&L.ctl->flags[pass % 3];
       if (!f) break;

@@ -197,8 +197,6 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-// A spin on another CTA gives up after this long and records GEO_ERR_TIMEOUT.
-constexpr unsigned long long kWaitLimitNs = 4000000000ULL;  // 4 s
 
 __device__ __forceinline__ void record_status(int *status, int code) {
   atomicCAS(status, 0, code);
@@ -206,7 +204,8 @@ __device__ __forceinline__ void record_status(int *status, int code) {
 
 // Grid-wide barrier for a cooperative launch. Returns false (for every thread
 // of the CTA) if the wait expired or an error was already recorded.
-static __device__ __noinline__ bool grid_barrier(Control *ctl, int *status, unsigned nblocks) {
+static __device__ __noinline__ bool grid_barrier(Control *ctl, int *status, unsigned nblocks,
+                                                 unsigned long long limit_ns = kWaitLimitNs) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -223,7 +222,7 @@ static __device__ __noinline__ bool grid_barrier(Control *ctl, int *status, unsi
       unsigned spins = 0;
       while (ld_acquire_u32(&ctl->bar_gen) == gen) {
         if ((++spins & 63u) == 0) {
-          if (globaltimer_ns() - t0 > kWaitLimitNs) {
+          if (globaltimer_ns() - t0 > limit_ns) {
             record_status(status, GEO_ERR_TIMEOUT);
             ok = 0;
             break;
@@ -482,7 +481,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileLaunch L) {
     } else if (pass == L.npasses - 1) {
       break;
     }
-    if (!grid_barrier(L.ctl, L.status, gridDim.x)) return;
+    if (!grid_barrier(L.ctl, L.status, gridDim.x + (L.fault ? 1u : 0u), L.wait_ns)) return;
     if (rec) {
       const int f = *(volatile int *)&L.ctl->flags[pass % 3];
       if (!f) break;  // this pass changed nothing: fixed point reached
