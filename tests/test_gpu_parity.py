@@ -6,6 +6,7 @@ from the oracle only. Shapes span several tiles with ragged tails, single
 rows and columns, and step counts around the pass length.
 """
 import os
+import zlib
 
 import numpy as np
 import pytest
@@ -76,7 +77,7 @@ SHAPES = [(1, 1), (1, 37), (29, 1), (3, 5), (17, 33), (64, 64), (100, 77), (129,
 @pytest.mark.parametrize("op", ["dilate", "erode"])
 @pytest.mark.parametrize("conn", [4, 8])
 def test_chain_parity_shapes_and_lengths(kind, op, conn, kernel):
-    rng = np.random.default_rng(hash((kind, op, conn)) % 2**32)
+    rng = np.random.default_rng(zlib.crc32(f"{kind} {op} {conn}".encode()))
     m = gm()
     fn = m.dilate_chain if op == "dilate" else m.erode_chain
     for H, W in SHAPES:
@@ -173,3 +174,27 @@ def test_full_size_1024_u8_chain(kernel):
         got = host(fn(dev(w[key]), dev(w["mask"]), 100, conn=8))
         # full image for 100 steps
         assert_same(got, oracle.chain(w[key], w["mask"], 100, conn=8, op=op), f"1024 {op} 100")
+
+
+def test_random_shape_sweep():
+    """Seeded sweep: shapes with sides 1, 2, 3 and non-multiples of 4 / 16 /
+    32 (including K larger than the image), every dtype, op and
+    connectivity, chain lengths 0, 1, K - 1, K, K + 1 and 2K + 3 around the
+    planned pass length K."""
+    m = gm()
+    rng = np.random.default_rng(0x5EED)
+    sides = [1, 2, 3, 5, 7, 15, 31, 33, 47, 63, 65, 97, 131, 200, 301]
+    for case in range(24):
+        H, W = int(rng.choice(sides)), int(rng.choice(sides))
+        kind = ["u8", "f32", "f64"][case % 3]
+        op = "dilate" if (case // 3) % 2 == 0 else "erode"
+        conn = 8 if (case // 6) % 2 == 0 else 4
+        f, msk = rand_pair(H, W, kind, rng, op)
+        dt = {"u8": torch.uint8, "f32": torch.float32, "f64": torch.float64}[kind]
+        K, _, _ = m.plan_info(dt, op + "_chain", conn, H, W, 64)
+        fn = m.dilate_chain if op == "dilate" else m.erode_chain
+        for steps in sorted({0, 1, max(K - 1, 0), K, K + 1, 2 * K + 3}):
+            got = host(fn(dev(f), dev(msk), steps, conn=conn))
+            assert_same(got, oracle.chain(f, msk, steps, conn=conn, op=op),
+                        f"{kind} {op} conn{conn} {H}x{W} K={K} steps={steps}")
+    assert m.device_status() == 0

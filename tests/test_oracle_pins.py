@@ -190,6 +190,35 @@ def test_four_connected_chain_is_clipped_diamond(op):
                                       g(f, footprint=fp, mode="nearest"))
 
 
+def van_herk_1d(x, s, op, axis):
+    """Running extreme of window 2s+1 along `axis` by the van Herk / Gil-Werman
+    method: pad with the identity, cut into blocks of the window length, take
+    the prefix extreme g and the suffix extreme h inside every block; the
+    window starting at i is then ext(h[i], g[i + 2s])."""
+    ext = np.maximum if op == "dilate" else np.minimum
+    ident = -np.inf if op == "dilate" else np.inf
+    x = np.moveaxis(np.asarray(x, np.float64), axis, -1)
+    n, w = x.shape[-1], 2 * s + 1
+    nb = -(-(n + 2 * s) // w)
+    xp = np.full(x.shape[:-1] + (nb * w,), ident)
+    xp[..., s:s + n] = x
+    blocks = xp.reshape(x.shape[:-1] + (nb, w))
+    g = ext.accumulate(blocks, axis=-1).reshape(xp.shape)
+    h = ext.accumulate(blocks[..., ::-1], axis=-1)[..., ::-1].reshape(xp.shape)
+    i = np.arange(n)
+    return np.moveaxis(ext(h[..., i], g[..., i + w - 1]), -1, axis)
+
+
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+def test_window_matches_van_herk_at_full_size(op):
+    """The 1024x1024 workload-1 windows (s = 13 and 91) against a separable
+    van Herk / Gil-Werman running extreme, rows then columns."""
+    g = synth.workload1_u8()["mask"]
+    for s in (13, 91):
+        ref = van_herk_1d(van_herk_1d(g, s, op, 1), s, op, 0)
+        np.testing.assert_array_equal(oracle.window(g, s, op).astype(np.float64), ref)
+
+
 def test_window_on_workload_image():
     g = synth.workload0(96, 80)["mask"]
     for s in (13, 40):
