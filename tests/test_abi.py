@@ -80,3 +80,29 @@ def test_tune_cache_file_round_trip(tmp_path):
     import pytest as _pt
     with _pt.raises(gm.GeoError):
         gm.tune_load(bad)
+
+
+def test_missing_library_fails_loudly():
+    """No CPU fallback: when the CUDA library cannot be loaded, the first call
+    raises instead of computing anything."""
+    import subprocess
+    import sys
+    code = ("import torch, paper_1911_13074_gb300 as m\n"
+            "m.dilate_chain(torch.zeros(4, 4, dtype=torch.uint8), torch.zeros(4, 4, dtype=torch.uint8), 3)\n")
+    env = dict(os.environ, GEOMORPH_LIB=os.path.join(ROOT, "no_such_dir", "libgeomorph.so"))
+    p = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert p.returncode != 0
+    assert "OSError" in p.stderr or "TypeError" in p.stderr
+    code2 = "import paper_1911_13074_gb300 as m\nm.load()\n"
+    p = subprocess.run([sys.executable, "-c", code2], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert p.returncode != 0 and "OSError" in p.stderr
+
+
+def test_cpu_tensors_are_rejected():
+    import torch
+    import paper_1911_13074_gb300 as m
+    a = torch.zeros(4, 4, dtype=torch.uint8)
+    with pytest.raises(TypeError):
+        m.dilate_chain(a, a, 3)
+    with pytest.raises(TypeError):
+        m.qdt(a)
