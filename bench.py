@@ -7,6 +7,9 @@ entry point geo_dilate_chain. The metric is Gpixel-steps/s =
 H * W * chain_steps / seconds / 1e9, summed over all ranks (replicas).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py --only {batched,fwd_bwd,reconstruct_4096,operators,workload1}
+
+--only runs one of the secondary measurements alone (for profiler captures).
 
 --impl reference times the CPU oracle (the plain C loops of oracle/) on the
 host cores instead, on a bounded number of chain steps per bench step.
@@ -43,6 +46,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-secondary", action="store_true",
                    help="skip the batched and forward+backward comparisons")
+    p.add_argument("--only", default=None, choices=["batched", "fwd_bwd", "reconstruct_4096", "operators",
+                                                    "workload1"],
+                   help="run one secondary measurement alone (for profiler captures) and print it")
     p.add_argument("--chain-steps", type=int, default=CHAIN_STEPS,
                    help="chain length of a bench step (default 1500; shorter only for small profiler captures, "
                         "and then named in the output's config)")
@@ -244,13 +250,12 @@ def _time(fn, reps, warmup=1):
     return e0.elapsed_time(e1) / 1e3 / reps
 
 
-def secondary(dev):
-    """The batched and forward+backward forms against the plain path, same GPU."""
+def part_batched(dev):
+    """Workload 3 (512 items) in one launch vs 512 single-item calls."""
     import torch
     import paper_1911_13074_gb300 as gm
     import synth
     res = {}
-    # batched: workload 3 (512 items) in one launch vs 512 single-item calls
     w3 = synth.workload3()
     items = []
     for it in w3:
@@ -280,7 +285,15 @@ def secondary(dev):
         "gpu_launches_batched": 2, "gpu_launches_plain": len(items)}
     del items, batch, w3
     torch.cuda.empty_cache()
-    # forward + backward: workload 4 (32 x 512^2 f32, 256 steps) vs the plain forward
+    return res
+
+
+def part_fwd_bwd(dev):
+    """Workload 4 (32 x 512^2 f32, 256 steps) forward + backward vs the plain forward."""
+    import torch
+    import paper_1911_13074_gb300 as gm
+    import synth
+    res = {}
     w4 = synth.workload4()
     mk, ms, g = (torch.from_numpy(w4[k]).to(dev) for k in ("marker", "mask", "grad_out"))
     steps = 256
@@ -306,7 +319,14 @@ def secondary(dev):
     }
     del mk, ms, g, w4
     torch.cuda.empty_cache()
-    # reconstruction to stability: workload 2 (4096^2 blob masks), both markers
+    return res
+
+
+def part_reconstruct_4096(dev):
+    """Workload 2 (4096^2 blob masks): dilation by reconstruction to stability, both markers."""
+    import torch
+    import paper_1911_13074_gb300 as gm
+    import synth
     w2 = synth.workload2()
     rec = {}
     for kind in ("u8", "f32"):
@@ -324,7 +344,21 @@ def secondary(dev):
             n = int(steps_box["s"].item())
             rec[f"{kind}_{name}"] = {"ms": t * 1e3, "steps_applied": n,
                                      "gpixel_steps_per_s": mask.numel() * n / t / 1e9}
-    # geodesic operators of the paper's Table 5 on the 1024^2 u8 workload-1 image
+    res = {"reconstruct_4096": {
+        "workload": "4096x4096 blob masks (synthetic workload 2), 8-connected dilation by reconstruction to "
+                    "stability; steps_applied counts whole passes up to the first unchanged pass",
+        **rec}}
+    del w2
+    torch.cuda.empty_cache()
+    return res
+
+
+def part_operators(dev):
+    """The geodesic operators of the paper's Table 5 on the 1024^2 u8 workload-1 image."""
+    import torch
+    import paper_1911_13074_gb300 as gm
+    import synth
+    res = {}
     g = torch.from_numpy(synth.workload1_u8()["mask"]).to(dev)
     ops = {"hmax_h20": lambda: gm.hmax(g, 20), "dome_h20": lambda: gm.dome(g, 20), "hfill": lambda: gm.hfill(g),
            "raobj": lambda: gm.raobj(g), "open_rec_s15": lambda: gm.open_rec(g, 15),
@@ -332,10 +366,46 @@ def secondary(dev):
            "asf_11": lambda: gm.asf(g, 11)}
     res["operators_1024_u8"] = {"workload": "1024x1024 u8 workload-1 image, 8-connected",
                                 **{k: {"ms": _time(fn, 3) * 1e3} for k, fn in ops.items()}}
-    res["reconstruct_4096"] = {
-        "workload": "4096x4096 blob masks (synthetic workload 2), 8-connected dilation by reconstruction to "
-                    "stability; steps_applied counts whole passes up to the first unchanged pass",
-        **rec}
+    return res
+
+
+def part_workload1(dev):
+    """Every workload-1 case at 1024^2: chains of u8 and f64, both operations
+    and connectivities, 100 / 500 / 1500 steps, and the windows s = 13, 91."""
+    import torch
+    import paper_1911_13074_gb300 as gm
+    import synth
+    res = {}
+    for kind, w in (("u8", synth.workload1_u8()), ("f64", synth.workload1_f64())):
+        mask = torch.from_numpy(w["mask"]).to(dev)
+        out = torch.empty_like(mask)
+        for op in ("dilate", "erode"):
+            mk = torch.from_numpy(w["marker_" + op]).to(dev)
+            fn = gm.dilate_chain if op == "dilate" else gm.erode_chain
+            for conn in (4, 8):
+                for n in (100, 500, 1500):
+                    t = _time(lambda: fn(mk, mask, n, conn=conn, out=out), 2)
+                    res[f"chain_{kind}_{op}_conn{conn}_steps{n}"] = {
+                        "ms": t * 1e3, "gpixel_steps_per_s": mask.numel() * n / t / 1e9}
+            win = gm.window_dilate if op == "dilate" else gm.window_erode
+            for s in (13, 91):
+                t = _time(lambda: win(mask, s, out=out), 2)
+                res[f"window_{kind}_{op}_s{s}"] = {"ms": t * 1e3,
+                                                   "gpixel_steps_per_s": mask.numel() * s / t / 1e9}
+    return {"workload1_1024": {"workload": "1024x1024 synthetic workload 1 (u8 and f64), every chain and window "
+                                           "case; L2 not flushed between repetitions", **res}}
+
+
+PARTS = {"batched": part_batched, "fwd_bwd": part_fwd_bwd, "reconstruct_4096": part_reconstruct_4096,
+         "operators": part_operators, "workload1": part_workload1}
+
+
+def secondary(dev):
+    """The batched and forward+backward forms against the plain path, and the
+    other workloads, on the same GPU."""
+    res = {}
+    for fn in PARTS.values():
+        res.update(fn(dev))
     return res
 
 
@@ -355,6 +425,10 @@ def main():
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    if args.only:
+        if rank == 0:
+            print(json.dumps({"part": args.only, **PARTS[args.only](dev)}), flush=True)
+        return
     w = synth.workload1_u8(H, W)
     marker_h = torch.from_numpy(w["marker_dilate"]).pin_memory()
     mask_h = torch.from_numpy(w["mask"]).pin_memory()
