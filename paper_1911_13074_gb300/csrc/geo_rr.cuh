@@ -1,10 +1,13 @@
 // Register-resident, temporally blocked kernel for geodesic 3x3 chains.
 //
-// Same pass structure as the shared-memory tile kernel (geo_tile.cuh): one
-// cooperative persistent launch per chain (Eq. 4) or reconstruction (Eq. 5),
-// K steps per pass on a tile plus a K-pixel halo, grid barrier between
-// passes, per-pass "changed" flag for reconstruction. What differs is where
-// the tile lives during the K steps: in registers.
+// One cooperative persistent launch per chain (Eq. 4), window (Eq. 1-2) or
+// reconstruction (Eq. 5), K steps per pass on a tile plus a K-pixel halo, as
+// in the shared-memory tile kernel (geo_tile.cuh); what differs is where the
+// tile lives during the K steps: in registers. Chain passes synchronise
+// point to point (a tile waits for the 8 tiles its halo reads to publish the
+// previous pass); reconstruction passes meet at a grid barrier, test a
+// per-pass "changed" flag, and skip tiles whose 3x3 tile neighbourhood did
+// not change in the previous pass.
 //
 //   * A CTA holds a region of (32 * CW) x (NW * PH) pixels: warp w owns a
 //     horizontal band of PH pixel rows, lane l owns CW adjacent columns of it.
@@ -14,9 +17,10 @@
 //     the rows just above and below the band come from the adjacent warps
 //     through a small shared-memory exchange, once per step (one barrier).
 //   * uint8 pixels are "sliced": a 32-bit word holds the pixels of one column
-//     at rows r and r + RW of the band as two u16 lanes, so one max.u16x2
-//     decides two pixels and no byte shifts are needed except at the seam
-//     between the two halves of the band (one funnel shift per column).
+//     at rows r and r + RW of the band as two 16-bit lanes, so one packed
+//     max / min (f16x2 or u16x2, see GEO_RR_U8_F16) decides two pixels and no
+//     byte shifts are needed except at the seam between the two halves of
+//     the band (one funnel shift per column).
 //   * The step itself is Section 3.1's decomposition: row 3-extreme (h),
 //     column 3-extreme of h (8-conn) or of {f above, h, f below} (4-conn),
 //     then the mask clamp of Eq. 3, computed in place top to bottom with the
