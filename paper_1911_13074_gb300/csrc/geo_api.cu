@@ -373,6 +373,11 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
                : GEO_ERR_CUDA;
   }
 
+  // float64: long chains and reconstructions run on the ranks of the values
+  if (dt == GEO_F64 && batch == 1 && fault == FAULT_NONE && rank_path_applies(H, W, mask != nullptr, mode, steps))
+    return run_chain_ranked((const double *)marker, (const double *)mask, (double *)out, H, W, pitch, conn, op, mode,
+                            steps, steps_out, stream);
+
   DeviceState *ds = nullptr;
   int rc = device_state(&ds);
   if (rc != GEO_OK) return rc;

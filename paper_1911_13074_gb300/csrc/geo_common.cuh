@@ -114,6 +114,11 @@ int launch_plan(int dt, const TileLaunch &L, int op, int conn, cudaStream_t s, c
 // check of dt against the public geo_dtype values).
 int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64_t H, int64_t W, int64_t pitch,
                   int conn, int op, int mode, int64_t steps, int64_t *steps_out, void *stream, int batch);
+// float64 through the rank transform (geo_rank.cu): whether it applies
+// (size, chain length, GEOMORPH_F64=keys|ranks), and the driver.
+bool rank_path_applies(int64_t H, int64_t W, bool has_mask, int mode, int64_t steps);
+int run_chain_ranked(const double *marker, const double *mask, double *out, int64_t H, int64_t W, int64_t pitch,
+                     int conn, int op, int mode, int64_t steps, int64_t *steps_out, void *stream);
 // Cached plan of the register-resident kernel for an element type, op, item
 // code (0..5 as geo_item.op, for the tune cache) and chain length hint.
 int plan_rr(int dt, int op, int code, int conn, int64_t H, int64_t W, int64_t steps_hint, Plan *P);

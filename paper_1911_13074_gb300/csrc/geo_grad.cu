@@ -346,10 +346,6 @@ Layout layout(int es, int64_t H, int64_t W, int64_t steps, int C, int batch) {
   return L;
 }
 
-dim3 step_grid(int64_t H, int64_t W, int batch) {
-  return dim3((unsigned)((W + kBX - 1) / kBX), (unsigned)((H + kBY - 1) / kBY), (unsigned)batch);
-}
-
 template <typename T, int TT>
 int launch_seg(int op, int conn, const T *f0, const T *mask, int64_t mpitch, const T *gin, int64_t gi_pitch, T *gout,
                int64_t go_pitch, T *gm, int64_t gm_pitch, int H, int W, int batch, int S, int first, cudaStream_t s) {

@@ -360,6 +360,7 @@ struct RR {
         // values live at once (f32 / f64 hold 8 rows per lane; f64 words
         // take two registers each)
         constexpr int CH = sizeof(Wd) == 8 ? 1 : 4;
+        static_assert(RW % CH == 0, "word rows come in whole chunks");
 #pragma unroll
         for (int r0 = 0; r0 < RW; r0 += CH) {
           typename P::Raw raw[CH];
@@ -367,12 +368,11 @@ struct RR {
 #pragma unroll
           for (int i = 0; i < CH; ++i) {
             const int64_t gy = gy0 + r0 + i;
-            in[i] = r0 + i < RW && cols_in && gy >= 0 && gy < H;
+            in[i] = cols_in && gy >= 0 && gy < H;
             if (in[i]) raw[i] = P::load_raw(Q.ptr + gy * Q.pitch_b + gx * GS, cg);
           }
 #pragma unroll
           for (int i = 0; i < CH; ++i) {
-            if (r0 + i >= RW) break;
             Px v[CW];
             P::unpack_raw(raw[i], v);
 #pragma unroll
@@ -380,37 +380,30 @@ struct RR {
           }
         }
         return;
-      }
-      typename P::Raw raw[B * RW];
-      bool in[B * RW];
+      } else {
+        // two rows per word: every row's load first, then the words
+        typename P::Raw raw[B * RW];
+        bool in[B * RW];
 #pragma unroll
-      for (int i = 0; i < B * RW; ++i) {
-        const int64_t gy = gy0 + i;
-        in[i] = cols_in && gy >= 0 && gy < H;
-        if (in[i]) raw[i] = P::load_raw(Q.ptr + gy * Q.pitch_b + gx * GS, cg);
-      }
-#pragma unroll
-      for (int r = 0; r < RW; ++r) {
-        Px lo[CW], hi[CW];
-        P::unpack_raw(raw[r], lo);
-        if (!in[r]) {
-#pragma unroll
-          for (int c = 0; c < CW; ++c) lo[c] = P::ident();
+        for (int i = 0; i < B * RW; ++i) {
+          const int64_t gy = gy0 + i;
+          in[i] = cols_in && gy >= 0 && gy < H;
+          if (in[i]) raw[i] = P::load_raw(Q.ptr + gy * Q.pitch_b + gx * GS, cg);
         }
-        if constexpr (B == 2) {
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+          Px lo[CW], hi[CW];
+          P::unpack_raw(raw[r], lo);
           P::unpack_raw(raw[RW + r], hi);
-          if (!in[RW + r]) {
 #pragma unroll
-            for (int c = 0; c < CW; ++c) hi[c] = P::ident();
+          for (int c = 0; c < CW; ++c) {
+            if (!in[r]) lo[c] = P::ident();
+            if (!in[RW + r]) hi[c] = P::ident();
+            w[r][c] = P::make(lo[c], hi[c]);
           }
-        } else {
-#pragma unroll
-          for (int c = 0; c < CW; ++c) hi[c] = lo[c];
         }
-#pragma unroll
-        for (int c = 0; c < CW; ++c) w[r][c] = P::make(lo[c], hi[c]);
+        return;
       }
-      return;
     }
 #pragma unroll
     for (int r = 0; r < RW; ++r) {

@@ -40,7 +40,12 @@ def sha(t):
     return hashlib.sha256(np.ascontiguousarray(t.cpu().numpy()).tobytes()).hexdigest()
 
 
-def test_workload1_full_size_against_oracle_digests():
+@pytest.mark.parametrize("f64_path", ["auto", "keys"])
+def test_workload1_full_size_against_oracle_digests(f64_path, monkeypatch):
+    """All 32 cases; float64 chains of 500 and 1500 steps take the rank
+    transform by default, so they run once more on int64 keys."""
+    if f64_path == "keys":
+        monkeypatch.setenv("GEOMORPH_F64", "keys")
     cases = json.load(open(GOLDEN))["cases"]
     m = gm()
     data = {"u8": synth.workload1_u8(), "f64": synth.workload1_f64()}

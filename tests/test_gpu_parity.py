@@ -198,3 +198,40 @@ def test_random_shape_sweep():
             assert_same(got, oracle.chain(f, msk, steps, conn=conn, op=op),
                         f"{kind} {op} conn{conn} {H}x{W} K={K} steps={steps}")
     assert m.device_status() == 0
+
+
+@pytest.mark.parametrize("path", ["ranks", "keys"])
+@pytest.mark.parametrize("op", ["dilate", "erode"])
+def test_f64_rank_and_key_paths(path, op, monkeypatch):
+    """float64 long chains, windows and reconstructions run on the ranks of
+    the values (an order isomorphism) or on int64 keys; both must equal the
+    oracle bit for bit. Inputs mix many equal values, negative values and
+    values a few ulps apart."""
+    monkeypatch.setenv("GEOMORPH_F64", path)
+    m = gm()
+    rng = np.random.default_rng(0xF64)
+    for H, W in [(1, 1), (1, 300), (37, 1), (130, 97), (257, 190)]:
+        base = rng.integers(-40, 40, (H, W)).astype(np.float64) / 8.0      # many ties
+        jit = np.where(rng.random((H, W)) < 0.3, np.spacing(base) * rng.integers(1, 4, (H, W)), 0.0)
+        msk = base + jit
+        d = np.abs(rng.standard_normal((H, W)))
+        f = msk + d if op == "erode" else msk - d
+        fn = m.dilate_chain if op == "dilate" else m.erode_chain
+        for steps in (128, 200):
+            assert_same(host(fn(dev(f), dev(msk), steps, conn=8)), oracle.chain(f, msk, steps, conn=8, op=op),
+                        f"chain {path} {H}x{W} steps={steps}")
+        win = m.window_dilate if op == "dilate" else m.window_erode
+        assert_same(host(win(dev(msk), 130)), oracle.window(msk, 130, op=op), f"window {path} {H}x{W}")
+        rec = host(m.reconstruct(dev(f), dev(msk), conn=4, op=op))
+        assert_same(rec, oracle.reconstruct(f, msk, conn=4, op=op)[0], f"reconstruct {path} {H}x{W}")
+        # in place, and rows with a pitch larger than the width
+        t = dev(f)
+        fn(t, dev(msk), 150, conn=8, out=t)
+        assert_same(host(t), oracle.chain(f, msk, 150, conn=8, op=op), f"in place {path} {H}x{W}")
+        big = torch.zeros((H, W + 5), dtype=torch.float64, device=DEV)
+        big[:, :W] = dev(f)
+        bm = torch.zeros_like(big)
+        bm[:, :W] = dev(msk)
+        o = fn(big[:, :W], bm[:, :W], 140, conn=8)
+        assert_same(host(o), oracle.chain(f, msk, 140, conn=8, op=op), f"pitched {path} {H}x{W}")
+    assert m.device_status() == 0
