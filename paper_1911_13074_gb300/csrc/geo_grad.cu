@@ -317,7 +317,14 @@ __global__ void __launch_bounds__(kBX * kBY) zero_plane(T *__restrict__ p, int64
 }
 
 // Sub-segment length of the fused kernel and its tile side per element type.
-constexpr int kSeg = 8;
+// 8 steps measured best on workload 4 (17.2 ms forward + backward; 6 steps
+// 19.3 ms, 4 steps 20.6 ms: the halos shrink but launches and staging
+// double); longer sub-segments do not fit 227 KB of shared memory at a
+// 64-pixel tile.
+#ifndef GEO_SEG_STEPS
+#define GEO_SEG_STEPS 8
+#endif
+constexpr int kSeg = GEO_SEG_STEPS;
 constexpr int kTileF32 = 64, kTileF64 = 32;
 
 struct Layout {
