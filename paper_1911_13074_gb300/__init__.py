@@ -14,6 +14,7 @@ Operations (Zlaus & Mongus, IEEE TPDS 2019, Section 2):
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import threading
@@ -139,8 +140,22 @@ def _check(rc: int, where: str):
         raise GeoError(rc, where)
 
 
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
 def _stream(t: torch.Tensor) -> int:
+    """The raw handle of the current stream of t's device."""
+    if _raw_stream is not None:
+        return _raw_stream(t.device.index)
     return torch.cuda.current_stream(t.device).cuda_stream
+
+
+def _on(t: torch.Tensor):
+    """Context that makes t's device current (a no-op when it already is:
+    entering torch.cuda.device costs more than the launch of a short call)."""
+    if t.device.index == torch.cuda.current_device():
+        return contextlib.nullcontext()
+    return torch.cuda.device(t.device)
 
 
 def _image(t: torch.Tensor, name: str):
@@ -182,7 +197,7 @@ def _chain(name: str, marker, mask, steps: int, conn: int, out):
     _same(marker, mask, "mask")
     out = _out_like(marker, out)
     H, W = marker.shape
-    with torch.cuda.device(marker.device):
+    with _on(marker):
         rc = getattr(lib, name)(DTYPES[marker.dtype], marker.data_ptr(), mask.data_ptr(), out.data_ptr(),
                                 H, W, _pitch(marker), int(conn), int(steps), _stream(marker))
     _check(rc, name)
@@ -213,7 +228,7 @@ def reconstruct(marker: torch.Tensor, mask: torch.Tensor, conn: int = 8, op: str
     out = _out_like(marker, out)
     H, W = marker.shape
     steps = torch.zeros(1, dtype=torch.int64, device=marker.device) if return_steps else None
-    with torch.cuda.device(marker.device):
+    with _on(marker):
         rc = lib.geo_reconstruct(DTYPES[marker.dtype], marker.data_ptr(), mask.data_ptr(), out.data_ptr(),
                                  H, W, _pitch(marker), int(conn), {"dilate": 0, "erode": 1}[op], int(max_steps),
                                  None if steps is None else steps.data_ptr(), _stream(marker))
@@ -226,7 +241,7 @@ def _window(name: str, img, half_size: int, out):
     _image(img, "in")
     out = _out_like(img, out)
     H, W = img.shape
-    with torch.cuda.device(img.device):
+    with _on(img):
         rc = getattr(lib, name)(DTYPES[img.dtype], img.data_ptr(), out.data_ptr(), H, W, _pitch(img),
                                 int(half_size), _stream(img))
     _check(rc, name)
@@ -287,7 +302,7 @@ def chain_fwd_ckpt(marker, mask, steps: int, conn: int = 8, op: str = "dilate", 
         raise GeoError(-1, "geo_chain_backward_workspace_size")
     ws = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=mk.device)
     out = torch.empty_like(mk)
-    with torch.cuda.device(mk.device):
+    with _on(mk):
         rc = lib.geo_chain_fwd_ckpt(dt, _OPS[op], mk.data_ptr(), ms.data_ptr(), out.data_ptr(), H, W, W, int(conn),
                                     int(steps), int(ckpt_interval), B, ws.data_ptr(), int(nbytes), _stream(mk))
     _check(rc, "geo_chain_fwd_ckpt")
@@ -303,7 +318,7 @@ def chain_backward(mask, grad_out, workspace, steps: int, conn: int = 8, op: str
     B, H, W = ms.shape
     gmk = torch.empty_like(ms)
     gms = torch.empty_like(ms)
-    with torch.cuda.device(ms.device):
+    with _on(ms):
         rc = lib.geo_chain_backward(DTYPES[ms.dtype], _OPS[op], ms.data_ptr(), g.data_ptr(), gmk.data_ptr(),
                                     gms.data_ptr(), H, W, W, int(conn), int(steps), int(ckpt_interval), B,
                                     workspace.data_ptr(), _stream(ms))
@@ -391,7 +406,7 @@ class Batch:
 
     def prepare(self):
         lib = load()
-        with torch.cuda.device(self.device):
+        with _on(self):
             rc = lib.geo_batch_prepare(self.items, self.n, self.workspace.data_ptr(), self.nbytes,
                                        torch.cuda.current_stream(self.device).cuda_stream)
         _check(rc, "geo_batch_prepare")
@@ -399,7 +414,7 @@ class Batch:
 
     def launch(self):
         lib = load()
-        with torch.cuda.device(self.device):
+        with _on(self):
             rc = lib.geo_batch_launch(self.items, self.n, self.workspace.data_ptr(), self.status.data_ptr(),
                                       torch.cuda.current_stream(self.device).cuda_stream)
         _check(rc, "geo_batch_launch")
@@ -419,7 +434,7 @@ def autotune(items, cache_path=None):
     keep the fastest in the library's tune table; write it to cache_path."""
     b = Batch(items)  # builds the geo_item array and output buffers
     lib = load()
-    with torch.cuda.device(b.device):
+    with _on(b):
         rc = lib.geo_autotune(b.items, b.n, None if cache_path is None else str(cache_path).encode())
     _check(rc, "geo_autotune")
     return b.outs
@@ -454,7 +469,7 @@ def _op(name, f, conn, *extra, out=None):
     _image(f, "f")
     out = _out_like(f, out)
     H, W = f.shape
-    with torch.cuda.device(f.device):
+    with _on(f):
         rc = getattr(lib, name)(DTYPES[f.dtype], f.data_ptr(), out.data_ptr(), H, W, _pitch(f), int(conn), *extra,
                                 _stream(f))
     _check(rc, name)
@@ -504,7 +519,7 @@ def qdt(f, conn=8, lipschitz=True):
     r = torch.empty_strided(f.shape, (pitch, 1), dtype=torch.uint8, device=f.device)
     d = torch.empty_strided(f.shape, (pitch, 1), dtype=torch.int32, device=f.device)
     dl1 = torch.empty_strided(f.shape, (pitch, 1), dtype=torch.int32, device=f.device) if lipschitz else None
-    with torch.cuda.device(f.device):
+    with _on(f):
         rc = lib.geo_qdt(DTYPES[f.dtype], f.data_ptr(), r.data_ptr(), d.data_ptr(),
                          dl1.data_ptr() if lipschitz else None, H, W, pitch, int(conn), _stream(f))
     _check(rc, "geo_qdt")
@@ -520,7 +535,7 @@ def _win(name, f, s, out):
     _image(f, "f")
     out = _out_like(f, out)
     H, W = f.shape
-    with torch.cuda.device(f.device):
+    with _on(f):
         rc = getattr(lib, name)(DTYPES[f.dtype], f.data_ptr(), out.data_ptr(), H, W, _pitch(f), int(s), _stream(f))
     _check(rc, name)
     return out
@@ -549,7 +564,7 @@ def granulometry(f, smax):
     H, W = f.shape
     G = torch.empty(int(smax) + 1, dtype=torch.float64, device=f.device)
     PS = torch.empty(max(int(smax), 1), dtype=torch.float64, device=f.device)
-    with torch.cuda.device(f.device):
+    with _on(f):
         rc = lib.geo_granulometry(DTYPES[f.dtype], f.data_ptr(), H, W, _pitch(f), int(smax), G.data_ptr(),
                                   PS.data_ptr(), _stream(f))
     _check(rc, "geo_granulometry")
