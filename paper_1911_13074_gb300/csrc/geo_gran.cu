@@ -1,26 +1,224 @@
 // Openings, closings, granulometry with its pattern spectrum, and alternating
-// sequential filters (Section 2, Eq. 16-20), composed from the unmasked 3x3
-// chains of the register-resident kernel (morph_window_erode / _dilate, s
-// elementary steps for a (2s+1)^2 square).
+// sequential filters (Section 2, Eq. 16-20), on the register engine's
+// unmasked 3x3 chains (s elementary steps for a (2s+1)^2 square).
 //
-// * gamma_s(f) = delta_s(eps_s(f)) and phi_s(f) = eps_s(delta_s(f)): two window
-//   calls, the second in place on the output.
-// * ASF_s = phi_s gamma_s ... phi_1 gamma_1 is the sequence of elementary
-//   steps E1 D1 D1 E1 E2 D2 D2 E2 ... Es Ds Ds Es (E = eps_1, D = delta_1,
-//   counts as written). Runs of the same operation are merged into one window
-//   call (E1, D2, E3, D4, ..., D2s, Es): the same steps in the same order,
-//   2s + 1 launches instead of 4s.
+// * gamma_s(f) = delta_s(eps_s(f)), phi_s(f) = eps_s(delta_s(f)) and
+//   ASF_s = phi_s gamma_s ... phi_1 gamma_1 are programs of runs of one
+//   operation (prog_kernel below), each one persistent launch. ASF_s is the
+//   sequence of elementary steps E1 D1 D1 E1 E2 D2 D2 E2 ... Es Ds Ds Es
+//   (E = eps_1, D = delta_1, counts as written); runs of the same operation
+//   are merged (E1, D2, E3, D4, ..., D2s, Es): the same steps in the same
+//   order.
 // * G_s = sum of gamma_s(f) for s = 0..smax: eps_s(f) is kept and eroded one
 //   more step for each s (eps_s = eps_1 eps_{s-1} by Eq. 4's nesting), the
 //   dilation of s steps goes to a second buffer, and a two-stage reduction
 //   sums it in double (fixed partition and order: deterministic; exact for
 //   uint8 images). PS_s = G_s - G_{s+1}.
 #include <cstring>
+#include <vector>
 
-#include "geo_common.cuh"
+#include "geo_rr.cuh"
 
 namespace geo {
 namespace {
+
+// ---------------------------------------------------------------------------
+// Programs of unmasked 8-connected runs (erode or dilate, n elementary steps
+// each) in one persistent launch of the register engine: the passes of all
+// runs are numbered in order and synchronised point to point through the
+// per-tile epochs exactly as one chain's passes are; each pass runs the
+// policy of its run, with the virtual mask and the exchange buffer's
+// identity rows of that operation.
+// ---------------------------------------------------------------------------
+
+constexpr int kMaxRuns = 48;
+
+struct Program {
+  int nruns;
+  int total_passes;
+  int op[kMaxRuns];
+  int npasses[kMaxRuns];
+  int64_t steps[kMaxRuns];
+};
+
+template <class P>
+__device__ __forceinline__ bool prog_tile(const TileLaunch &L, const Plane &src, const Plane &dst, bool src_cg,
+                                          int64_t ty0, int64_t tx0, int S, typename P::Wd *xb0, int xb_stride,
+                                          uint64_t *bar, int &parity, int lane, int warp,
+                                          typename P::Wd (&w)[P::RW][P::CW], typename P::Wd (&m)[P::RW][P::CW]) {
+  using R = RR<P>;
+  const int K = L.K;
+  const int64_t gy0 = ty0 - K + warp * R::PH, gx = tx0 - K + lane * R::CW;
+  R::load_words(src, L.H, L.W, gy0, gx, src_cg, false, w);
+  R::load_words(src, L.H, L.W, gy0, gx, false, true, m);  // the virtual mask of this operation
+  bool ok = true;
+  for (int j = 0; j < S; ++j) {
+    ok &= R::template step<8>(w, m, xb0 + (size_t)parity * xb_stride, bar, parity, lane, warp);
+    parity ^= 1;
+  }
+  R::store(w, dst, src, false, L.H, L.W, ty0, tx0, K, L.TH, L.TW, lane, warp);
+  return ok;
+}
+
+template <template <int> class RP>
+__global__ void __launch_bounds__(RP<DILATE>::NW * 32, 1) prog_kernel(const TileLaunch L, const Program G) {
+  using PD = RP<DILATE>;
+  using PE = RP<ERODE>;
+  using Wd = typename PD::Wd;
+  constexpr int CW = PD::CW, RW = PD::RW, NW = PD::NW, RWID = 32 * CW;
+  extern __shared__ __align__(16) char rr_dyn[];
+  Wd(*xbuf)[NW + 2][2][RWID] = reinterpret_cast<Wd(*)[NW + 2][2][RWID]>(rr_dyn);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ntiles = L.tiles_x * L.tiles_y;
+  __shared__ __align__(8) uint64_t xbar;
+  if (threadIdx.x == 0) mbar_init(&xbar, NW * 32);
+  Wd w[RW][CW], m[RW][CW];
+  int parity = 0, cur_op = -1, p = 0;
+  for (int r = 0; r < G.nruns; ++r) {
+    const int op = G.op[r];
+    if (op != cur_op) {
+      // the rows above warp 0 and below warp NW-1 hold this operation's identity
+      __syncthreads();
+      const Wd id = op == DILATE ? PD::identw() : PE::identw();
+      for (int i = threadIdx.x; i < 2 * 2 * RWID; i += NW * 32) {
+        const int par = i / (2 * RWID), rest = i % (2 * RWID);
+        (&xbuf[par][0][0][0])[rest] = id;
+        (&xbuf[par][NW + 1][0][0])[rest] = id;
+      }
+      __syncthreads();
+      cur_op = op;
+    }
+    const int np = G.npasses[r];
+    const int64_t base = np > 0 ? G.steps[r] / np : 0, extra = np > 0 ? G.steps[r] % np : 0;
+    for (int q = 0; q < np; ++q, ++p) {
+      const int S = (int)(base + (q < extra ? 1 : 0));
+      const bool to_out = ((G.total_passes - 1 - p) & 1) == 0;
+      const Plane dst = to_out ? L.out : L.scratch;
+      const Plane src = p == 0 ? L.marker : (to_out ? L.scratch : L.out);
+      const bool src_cg = p > 0 || L.marker.ptr == L.out.ptr;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int ty = t / L.tiles_x, tx = t - ty * L.tiles_x;
+        if (p > 0) {
+          if (warp == 0 &&
+              !wait_neighbours(L.epoch, ty, tx, L.tiles_y, L.tiles_x, L.fault ? p + (1 << 28) : p, lane,
+                               L.wait_ns) &&
+              lane == 0)
+            record_status(L.status, GEO_ERR_TIMEOUT);
+          __syncthreads();
+        }
+        const int64_t ty0 = (int64_t)ty * L.TH, tx0 = (int64_t)tx * L.TW;
+        const bool ok = op == DILATE ? prog_tile<PD>(L, src, dst, src_cg, ty0, tx0, S, &xbuf[0][0][0][0],
+                                                     (NW + 2) * 2 * RWID, &xbar, parity, lane, warp, w, m)
+                                     : prog_tile<PE>(L, src, dst, src_cg, ty0, tx0, S, &xbuf[0][0][0][0],
+                                                     (NW + 2) * 2 * RWID, &xbar, parity, lane, warp, w, m);
+        if (!ok) record_status(L.status, GEO_ERR_TIMEOUT);
+        if (p + 1 < G.total_passes) {
+          __syncthreads();
+          if (threadIdx.x == 0) st_release_u32(reinterpret_cast<unsigned *>(L.epoch) + t, (unsigned)(p + 1));
+        }
+      }
+    }
+  }
+}
+
+template <template <int> class RP>
+int launch_prog(const TileLaunch &L, const Program &G, int grid, cudaStream_t s) {
+  void *k = (void *)prog_kernel<RP>;
+  const size_t smem = rr_smem_bytes<RP<DILATE>>();
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return GEO_ERR_CUDA;
+  TileLaunch a = L;
+  Program g = G;
+  void *args[] = {(void *)&a, (void *)&g};
+  return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(RP<DILATE>::NW * 32), args, smem, s) == cudaSuccess
+             ? GEO_OK
+             : GEO_ERR_CUDA;
+}
+
+Plane prog_plane(const void *p, int64_t pitch_b, size_t va) {
+  Plane q;
+  q.ptr = (char *)p;
+  q.pitch_b = pitch_b;
+  q.vec_ok = (p != nullptr && ((uintptr_t)p % va) == 0 && pitch_b % (int64_t)va == 0) ? 1 : 0;
+  q.bstride = 0;
+  return q;
+}
+
+// Run the unmasked 8-connected runs (op[i], steps[i]) on f into out (which
+// may equal f), at most kMaxRuns per launch.
+int run_program(int dt, const void *f, void *out, int64_t H, int64_t W, int64_t pitch, const int *ops,
+                const int64_t *steps, int nruns, cudaStream_t s) {
+  int64_t total = 0;
+  for (int i = 0; i < nruns; ++i) total += steps[i];
+  Plan P;
+  int rc = plan_rr(dt, DILATE, 4, 8, H, W, total, &P);
+  if (rc != GEO_OK) return rc;
+  int *status = nullptr;
+  rc = device_status_word(&status);
+  if (rc != GEO_OK) return rc;
+  const int es = dt == GEO_U8 ? 1 : dt == GEO_F32 ? 4 : 8;
+  const size_t va = (size_t)(dt == GEO_F64 ? 2 : 4) * es;  // the register kernel's CW pixels
+  const int64_t spitch_b = ((W * es + 15) / 16) * 16;
+  const size_t ntiles = (size_t)P.tiles_x * P.tiles_y;
+  const size_t ctl_b = 256 + ((ntiles * sizeof(int) + 255) / 256) * 256;
+  void *scratch = nullptr;
+  rc = pool_alloc(&scratch, ctl_b + (size_t)spitch_b * H, s);
+  if (rc != GEO_OK) return rc;
+  const void *src = f;
+  for (int r0 = 0; r0 < nruns && rc == GEO_OK; r0 += kMaxRuns) {
+    Program G;
+    memset(&G, 0, sizeof(G));
+    for (int i = r0; i < nruns && G.nruns < kMaxRuns; ++i) {
+      G.op[G.nruns] = ops[i];
+      G.steps[G.nruns] = steps[i];
+      G.npasses[G.nruns] = (int)((steps[i] + P.K - 1) / P.K);
+      G.total_passes += G.npasses[G.nruns];
+      ++G.nruns;
+    }
+    if (G.total_passes == 0) {
+      if (src != out &&
+          cudaMemcpy2DAsync(out, pitch * es, src, pitch * es, W * es, H, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        rc = GEO_ERR_CUDA;
+      src = out;
+      continue;
+    }
+    // in place: the first pass must not write the buffer it reads, so the
+    // pass count must be even (the last run takes one more, shorter pass)
+    if (src == out && (G.total_passes & 1)) {
+      ++G.npasses[G.nruns - 1];
+      ++G.total_passes;
+    }
+    if (cudaMemsetAsync(scratch, 0, ctl_b, s) != cudaSuccess) {
+      rc = GEO_ERR_CUDA;
+      break;
+    }
+    TileLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.marker = prog_plane(src, pitch * es, va);
+    L.mask = prog_plane(nullptr, 0, 1);
+    L.out = prog_plane(out, pitch * es, va);
+    L.scratch = prog_plane((char *)scratch + ctl_b, spitch_b, va);
+    L.H = H;
+    L.W = W;
+    L.TH = P.TH;
+    L.TW = P.TW;
+    L.K = P.K;
+    L.tiles_x = P.tiles_x;
+    L.tiles_y = P.tiles_y;
+    L.mode = MODE_CHAIN;
+    L.batch = 1;
+    L.epoch = (int *)((char *)scratch + 256);
+    L.ctl = (Control *)scratch;
+    L.status = status;
+    L.wait_ns = kWaitLimitNs;
+    rc = dt == GEO_U8 ? launch_prog<SU8>(L, G, P.grid, s)
+         : dt == GEO_F32 ? launch_prog<SF32>(L, G, P.grid, s)
+                         : launch_prog<SF64>(L, G, P.grid, s);
+    src = out;
+  }
+  if (pool_free(scratch, s) != GEO_OK && rc == GEO_OK) rc = GEO_ERR_CUDA;
+  return rc;
+}
 
 constexpr int kSumBlocks = 1024, kSumThreads = 256;
 
@@ -93,9 +291,9 @@ int open_close(int first, geo_dtype dt, const void *f, void *out, int64_t H, int
   if (!f || !out) return GEO_ERR_ARG;
   const size_t span = (size_t)((H - 1) * pitch + W) * elem_bytes(dt);
   if (f != out && overlap(f, out, span)) return GEO_ERR_ARG;
-  int rc = window(first, dt, f, out, H, W, pitch, s, stream);
-  if (rc == GEO_OK) rc = window(first == ERODE ? DILATE : ERODE, dt, out, out, H, W, pitch, s, stream);
-  return rc;
+  const int ops[2] = {first, first == ERODE ? DILATE : ERODE};
+  const int64_t steps[2] = {s, s};
+  return run_program(dt, f, out, H, W, pitch, ops, steps, 2, (cudaStream_t)stream);
 }
 
 }  // namespace
@@ -133,30 +331,27 @@ int geo_asf(geo_dtype dtype, const void *f, void *out, int64_t height, int64_t w
                : GEO_ERR_CUDA;
   }
   // level k contributes the runs E k, D k, D k, E k; equal neighbours merge,
-  // which leaves E 1, D 2, E 3, D 4, ..., D 2s, E s
-  int rc = GEO_OK;
-  const void *src = f;
+  // which leaves E 1, D 2, E 3, D 4, ..., D 2s, E s, all in one program
+  std::vector<int> ops;
+  std::vector<int64_t> steps;
   int cur_op = ERODE;
   int64_t run = 0;
-  auto flush = [&](int op, int64_t n) {
-    if (rc != GEO_OK || n == 0) return;
-    rc = window(op, dtype, src, out, H, W, pitch, n, stream);
-    src = out;
-  };
   for (int64_t k = 1; k <= s; ++k) {
     const int seq[4] = {ERODE, DILATE, DILATE, ERODE};
     for (int i = 0; i < 4; ++i) {
       if (seq[i] == cur_op) {
         run += k;
       } else {
-        flush(cur_op, run);
+        ops.push_back(cur_op);
+        steps.push_back(run);
         cur_op = seq[i];
         run = k;
       }
     }
   }
-  flush(cur_op, run);
-  return rc;
+  ops.push_back(cur_op);
+  steps.push_back(run);
+  return run_program(dtype, f, out, H, W, pitch, ops.data(), steps.data(), (int)ops.size(), (cudaStream_t)stream);
 }
 
 int geo_granulometry(geo_dtype dtype, const void *f, int64_t height, int64_t width, int64_t pitch, int64_t smax,
