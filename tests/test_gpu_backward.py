@@ -118,3 +118,27 @@ def test_backward_rejects_u8():
     x = torch.zeros(8, 8, dtype=torch.uint8, device="cuda")
     assert lib.geo_chain_fwd_ckpt(0, 0, x.data_ptr(), x.data_ptr(), x.data_ptr(), 8, 8, 8, 8, 4, 2, 1,
                                   x.data_ptr(), 64, None) == -2
+
+
+def test_backward_workload4_full_batch_as_benchmarked():
+    """The benchmark's launch configuration: all 32 images of workload 4 in
+    one forward-with-checkpoints and one backward call (C = 16). Three
+    images against the oracle; every image equal to a single-image call."""
+    w = synth.workload4()
+    mod = gm()
+    f, m, g = (torch.from_numpy(w[k]).cuda() for k in ("marker", "mask", "grad_out"))
+    out, ws = mod.chain_fwd_ckpt(f, m, 256, conn=8, ckpt_interval=16)
+    gmk, gms = mod.chain_backward(m, g, ws, 256, conn=8, ckpt_interval=16)
+    torch.cuda.synchronize()
+    assert mod.device_status() == 0
+    for b in (0, 13, 31):
+        fb, mb, gb = w["marker"][b], w["mask"][b], w["grad_out"][b]
+        np.testing.assert_array_equal(out[b].cpu().numpy(), oracle.chain(fb, mb, 256))
+        rmk, rms = oracle.chain_backward(fb, mb, gb, 256)
+        amk, ams = oracle.chain_backward(fb, mb, np.abs(gb), 256)
+        check_close(gmk[b].cpu().numpy(), rmk, amk, 1e-5, f"batch image {b} grad_marker")
+        check_close(gms[b].cpu().numpy(), rms, ams, 1e-5, f"batch image {b} grad_mask")
+    for b in range(32):
+        o1, ws1 = mod.chain_fwd_ckpt(f[b:b + 1], m[b:b + 1], 256, conn=8, ckpt_interval=16)
+        k1, s1 = mod.chain_backward(m[b:b + 1], g[b:b + 1], ws1, 256, conn=8, ckpt_interval=16)
+        assert torch.equal(o1[0], out[b]) and torch.equal(k1[0], gmk[b]) and torch.equal(s1[0], gms[b]), b
