@@ -5,17 +5,23 @@ leg may import this package. The product path (``paper_1911_13074_gb300``)
 never imports it and has no CPU fallback.
 
 The arithmetic lives in ``oracle.c`` (plain C loops written from the paper's
-definitions, Section 2, Eq. 1-5; see the header of that file). This module
-builds it with gcc into ``oracle/_build/liboracle.so`` and converts numpy
-arrays to and from float64 around each call. uint8 and float32 values
-convert to float64 exactly and the forward operators only select, so the
-results convert back exactly.
+definitions: Section 2, Eq. 1-5 for windows, steps, chains and
+reconstruction, Eq. 6-12 for the geodesic operators, Eq. 13-15 and
+Algorithm 6 for the quasi-distance transform, Eq. 16-20 for openings,
+closings, granulometry and ASF, plus the reverse mode of the chain; see the
+header of that file). This module builds it with gcc into
+``oracle/_build/liboracle.so`` and converts numpy arrays to and from float64
+around each call. uint8 and float32 values convert to float64 exactly and
+the forward operators only select, so the results convert back exactly.
 
 Parity pins: every function is checked against independent results in
 ``tests/test_oracle_pins.py`` (brute-force windows, scipy's max/min filters,
-threshold decomposition with breadth-first search, a widest-path search for
-reconstruction, finite differences and a source-identity closed form for the
-backward pass).
+a van Herk / Gil-Werman running extreme, threshold decomposition with
+breadth-first search, a widest-path search for reconstruction, finite
+differences and a source-identity closed form for the backward pass),
+``tests/test_oracle_ops_pins.py``, ``tests/test_oracle_qdt_pins.py`` and
+``tests/test_oracle_gran_pins.py``; ``tests/test_oracle_mutants.py`` checks
+that the pins catch planted mistakes.
 """
 from __future__ import annotations
 
