@@ -1,7 +1,7 @@
 """CPU oracle for geodesic 3x3 chains -- TEST INFRASTRUCTURE ONLY.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
-leg may import this package. The product path (``paper_1911_13074_gb300``)
+and reference legs may import this package. The product path (``paper_1911_13074_gb300``)
 never imports it and has no CPU fallback.
 
 The arithmetic lives in ``oracle.c`` (plain C loops written from the paper's

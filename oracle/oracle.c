@@ -1,8 +1,8 @@
 /*
  * CPU oracle for geodesic 3x3 chains. TEST INFRASTRUCTURE ONLY.
  *
- * Only the tests, the smoke check and the benchmark's CPU-baseline leg call
- * this code. It shares nothing with the CUDA library (no header, no helper, no
+ * Only the tests, the smoke check and the benchmark's CPU-baseline and
+ * reference legs call this code. It shares nothing with the CUDA library (no header, no helper, no
  * constant) and is written as the plain definitions from Zlaus & Mongus,
  * "Efficient method for parallel computation of geodesic transformation on
  * CPU" (IEEE TPDS 2019):
