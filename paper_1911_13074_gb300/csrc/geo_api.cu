@@ -231,10 +231,15 @@ static int plan_rr_uncached(int dt, int op, int conn, int64_t H, int64_t W, int6
     const int TW = RWID - 2 * K, TH = RHGT - 2 * K;
     const int64_t tiles = cdiv(H, TH) * cdiv(W, TW) * batch;
     const double per_sm = (double)cdiv(tiles, nsm);
+    // one tile covering one image runs without pass boundaries (rr_passes)
+    const bool one = tiles == 1;
     double cost;
     if (steps_hint > 0) {
-      const double passes = (double)cdiv(steps_hint, K);
+      const double passes = one ? 1.0 : (double)cdiv(steps_hint, K);
       cost = passes * kSyncSteps * per_sm + per_sm * (double)steps_hint;
+    } else if (one) {
+      const double n = (double)(H > W ? H : W);
+      cost = n + kSoloRecSteps + (n / kSoloRecSteps + 2.0) * kSyncSteps;
     } else {
       // reconstruction: the step count is unknown; take the longest side as
       // its scale and charge the overshoot (the pass that ends past the fixed
@@ -431,7 +436,7 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
   L.fault = fault == FAULT_TIMEOUT ? 1 : 0;
   L.wait_ns = L.fault ? kFaultWaitNs : kWaitLimitNs;
   if (mode == MODE_CHAIN) {
-    int64_t np = cdiv(steps, P.K);
+    int64_t np = rr ? rr_passes(steps, single_tile(P, batch) ? 0 : P.K) : cdiv(steps, P.K);
     if (alias && (np & 1)) ++np;  // pass 0 must not write the buffer it reads
     L.npasses = (int)np;
   }

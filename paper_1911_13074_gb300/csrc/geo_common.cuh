@@ -84,12 +84,28 @@ struct TileLaunch {
                           // wait for something that never happens, expire and report GEO_ERR_TIMEOUT
 };
 
+// Passes of a chain of `steps` with halo K; K = 0 for a single-tile plan of
+// the register kernel. When one tile covers the image (one image, one tile),
+// every cell of its region outside the interior lies outside the image and
+// stays the identity step after step (the mask clamp pins it), and there is
+// no neighbouring tile to exchange with: the steps need no pass boundaries
+// at all. A chain then runs in one pass (split only so that a pass's step
+// count fits an int) and reconstruction tests for change every
+// kSoloRecSteps steps.
+constexpr int64_t kSoloPassSteps = (int64_t)1 << 30;
+constexpr int kSoloRecSteps = 64;
+__host__ __device__ inline int64_t rr_passes(int64_t steps, int K) {
+  const int64_t k = K > 0 ? (int64_t)K : kSoloPassSteps;
+  return (steps + k - 1) / k;
+}
+
 // Tile geometry of one launch: interior TH x TW, halo K, shared-memory row
 // stride rs, tile grid, CTA count and dynamic shared memory.
 struct Plan {
   int TH, TW, K, rs, tiles_x, tiles_y, grid;
   size_t smem;
 };
+inline bool single_tile(const Plan &P, int batch) { return batch <= 1 && P.tiles_x == 1 && P.tiles_y == 1; }
 
 // Tuned pass length K for an item-op code (0..5 as geo_item.op), or 0 when
 // the tune cache has no entry (geo_tune.cu).

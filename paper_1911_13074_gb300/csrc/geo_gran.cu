@@ -171,7 +171,7 @@ int run_program(int dt, const void *f, void *out, int64_t H, int64_t W, int64_t 
     for (int i = r0; i < nruns && G.nruns < kMaxRuns; ++i) {
       G.op[G.nruns] = ops[i];
       G.steps[G.nruns] = steps[i];
-      G.npasses[G.nruns] = (int)((steps[i] + P.K - 1) / P.K);
+      G.npasses[G.nruns] = (int)rr_passes(steps[i], single_tile(P, 1) ? 0 : P.K);
       G.total_passes += G.npasses[G.nruns];
       ++G.nruns;
     }

@@ -349,7 +349,7 @@ int geo_qdt(geo_dtype dtype, const void *f, void *r, int32_t *d, int32_t *d_l1, 
   L.tiles_y = P.tiles_y;
   L.mode = MODE_CHAIN;
   L.steps = S;
-  L.npasses = (int)((S + P.K - 1) / P.K);
+  L.npasses = (int)rr_passes(S, single_tile(P, 1) ? 0 : P.K);
   L.ctl = (Control *)scratch;
   L.epoch = (int *)((char *)scratch + 256);
   L.status = status;

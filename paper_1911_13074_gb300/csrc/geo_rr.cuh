@@ -667,7 +667,9 @@ __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
       const int64_t base = L.steps / L.npasses, extra = L.steps % L.npasses;
       S = (int)(base + (pass < extra ? 1 : 0));
     } else {
-      S = (int)(steps_left < (int64_t)K ? steps_left : (int64_t)K);
+      // one tile covering one image: no halo exchange, test every kSoloRecSteps steps
+      const int64_t Kp = (ntiles == 1) ? kSoloRecSteps : K;
+      S = (int)(steps_left < Kp ? steps_left : Kp);
     }
     const bool to_out = rec ? (((pass + L.alias) & 1) == 0) : (((L.npasses - 1 - pass) & 1) == 0);
     const Plane dstP = to_out ? L.out : L.scratch;
