@@ -33,7 +33,11 @@ struct RD32 {
   using G = int32_t;
   static constexpr int BANDS = 2, CW = 4, RW = GEO_RR_U8_RW, NW = GEO_RR_U8_NW, GS = 4;
   static constexpr uint32_t kIdent = 0x7fffu;  // above every distance, and +1 stays inside the lane
+  static constexpr bool PAIRS = true;
+  static constexpr int FMA = 0;
   __device__ static Wd e2(Wd a, Wd b) { return umin2(a, b); }
+  __device__ static Wd e2h(Wd a, Wd b) { return umin2(a, b); }
+  __device__ static Wd e2m(Wd a, Wd b) { return umin2(a, b); }
   __device__ static Wd ext3(Wd a, Wd b, Wd c) { return umin2(umin2(a, b), c); }
   __device__ static Wd ext3h(Wd a, Wd b, Wd c) { return ext3(a, b, c); }
   __device__ static Wd clamp(Wd v, Wd m) { return umax2(v, m); }
@@ -78,7 +82,9 @@ struct RD32 {
 
 namespace {
 
-using QP = SU8<ERODE>;  // the image of part 1: uint8, erosion, no mask
+// the image of part 1: uint8, erosion, no mask; the clamp runs on the FMA
+// pipe because the observer's key updates load the ALU pipe
+using QP = RU8<ERODE, GEO_RR_U8_RW, GEO_RR_U8_NW, 1>;
 
 // Residual/erosion keys of one lane's pixels: k[band][word row][column]. As
 // the step observer it folds each written word's two residuals into the

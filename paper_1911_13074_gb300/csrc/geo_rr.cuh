@@ -49,6 +49,30 @@ namespace geo {
 #ifndef GEO_RR_U8_F16
 #define GEO_RR_U8_F16 7
 #endif
+// Bit mask of where policies without a one-instruction 3-extreme share the
+// 2-extreme of a pair of neighbours between the two outputs that need it
+// (1: row extremes of the 4-connected step, 2: column extremes of the
+// 8-connected step). Measured on the 1024^2 u8 1500-step chains: the column
+// sharing takes the 8-connected chain from 0.777 to 0.753 ms, the row
+// sharing the 4-connected one from 0.83 to 0.80 ms; the row sharing in the
+// 8-connected step made it slower (0.81 ms), so that step does not use it.
+#ifndef GEO_RR_PAIRS
+#define GEO_RR_PAIRS 3
+#endif
+// Bit mask of the u8 step's min/max groups computed by f16 arithmetic on
+// the FMA pipe instead of one packed min/max on the ALU pipe (1: mask clamp,
+// 2: column extremes of the band's first and last rows, 4: column extremes
+// of the inner rows, 8: the shared row pairs of the column pass); each moved
+// min/max costs two dependent FMA-pipe instructions instead of one ALU
+// instruction. Measured on the 1024^2 u8 1500-step chains (ms, 8-conn /
+// 4-conn): none 0.759 / 0.800, 1: 0.761 / 0.857, 3: 0.814, 7: 0.872,
+// 15: 0.90, so the chains keep every min/max on the ALU pipe. The
+// quasi-distance transform's first part, whose step also updates the keys
+// of its observer on the ALU pipe, takes the clamp to the FMA pipe (1:
+// 0.85 -> 0.75 ms per transform at 1024^2); its policy sets that itself.
+#ifndef GEO_RR_U8_FMA
+#define GEO_RR_U8_FMA 0
+#endif
 __device__ __forceinline__ uint32_t hmax2(uint32_t a, uint32_t b) {
   uint32_t r;
   asm("max.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
@@ -59,22 +83,48 @@ __device__ __forceinline__ uint32_t hmin2(uint32_t a, uint32_t b) {
   asm("min.f16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
   return r;
 }
+// relu(a - b) on both f16 lanes (one fma.relu: b * -1 + a)
+__device__ __forceinline__ uint32_t hrelu_diff(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("fma.rn.relu.f16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(b), "r"(0xBC00BC00u), "r"(a));
+  return r;
+}
+__device__ __forceinline__ uint32_t hfma2(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+// max / min of u16 lanes holding 0..255 through f16 arithmetic: read as f16
+// these are +0 and positive subnormals k * 2^-24 (subnormals are kept by f16
+// arithmetic), every difference of two of them is exact, so
+//   max(a, b) = b + relu(a - b)   and   min(a, b) = a - relu(a - b)
+// hold exactly, and no -0 arises (an exact zero sum rounds to +0).
+__device__ __forceinline__ uint32_t fmax2_u8(uint32_t a, uint32_t b) {
+  return hfma2(hrelu_diff(a, b), 0x3C003C00u, b);
+}
+__device__ __forceinline__ uint32_t fmin2_u8(uint32_t a, uint32_t b) {
+  return hfma2(hrelu_diff(a, b), 0xBC00BC00u, a);
+}
 
-template <int OP, int RW_ = 4, int NW_ = 16>
+template <int OP, int RW_ = 4, int NW_ = 16, int FMA_ = GEO_RR_U8_FMA>
 struct RU8 {
   using Wd = uint32_t;  // two u16 lanes: rows r and r + RW of one column
   using Px = uint32_t;  // one pixel value (0..255)
   using G = uint8_t;
   static constexpr int BANDS = 2, CW = 4, RW = RW_, NW = NW_, GS = 1;
+  static constexpr bool PAIRS = true;  // no one-instruction 3-extreme
+  static constexpr int FMA = FMA_;     // groups of GEO_RR_U8_FMA on the FMA pipe
   __device__ static Wd e2i(Wd a, Wd b) { return OP == DILATE ? umax2(a, b) : umin2(a, b); }
   __device__ static Wd e2f(Wd a, Wd b) { return OP == DILATE ? hmax2(a, b) : hmin2(a, b); }
   __device__ static Wd e2(Wd a, Wd b) { return (GEO_RR_U8_F16 & 2) ? e2f(a, b) : e2i(a, b); }
+  // the same on the FMA pipe
+  __device__ static Wd e2m(Wd a, Wd b) { return OP == DILATE ? fmax2_u8(a, b) : fmin2_u8(a, b); }
   __device__ static Wd ext3(Wd a, Wd b, Wd c) { return e2(e2(a, b), c); }
-  // the row 3-extreme (hrow)
-  __device__ static Wd ext3h(Wd a, Wd b, Wd c) {
-    return (GEO_RR_U8_F16 & 1) ? e2f(e2f(a, b), c) : e2i(e2i(a, b), c);
-  }
+  // the 2-extreme of the row pass (hrow)
+  __device__ static Wd e2h(Wd a, Wd b) { return (GEO_RR_U8_F16 & 1) ? e2f(a, b) : e2i(a, b); }
+  __device__ static Wd ext3h(Wd a, Wd b, Wd c) { return e2h(e2h(a, b), c); }
   __device__ static Wd clamp(Wd v, Wd m) {
+    if (FMA & 1) return OP == DILATE ? fmin2_u8(v, m) : fmax2_u8(v, m);
     if (GEO_RR_U8_F16 & 4) return OP == DILATE ? hmin2(v, m) : hmax2(v, m);
     return OP == DILATE ? umin2(v, m) : umax2(v, m);
   }
@@ -135,7 +185,11 @@ struct RF32 {
   using Px = float;
   using G = float;
   static constexpr int BANDS = 1, CW = 4, RW = RW_, NW = NW_, GS = 4;
+  static constexpr bool PAIRS = false;  // three-input max.f32 / min.f32
+  static constexpr int FMA = 0;
   __device__ static Wd e2(Wd a, Wd b) { return OP == DILATE ? fmaxf(a, b) : fminf(a, b); }
+  __device__ static Wd e2h(Wd a, Wd b) { return e2(a, b); }
+  __device__ static Wd e2m(Wd a, Wd b) { return e2(a, b); }
   __device__ static Wd ext3(Wd a, Wd b, Wd c) { return OP == DILATE ? fmax3(a, b, c) : fmin3(a, b, c); }
   __device__ static Wd ext3h(Wd a, Wd b, Wd c) { return ext3(a, b, c); }
   __device__ static Wd clamp(Wd v, Wd m) { return OP == DILATE ? fminf(v, m) : fmaxf(v, m); }
@@ -191,7 +245,11 @@ struct RF64 {
   using Px = long long;
   using G = double;
   static constexpr int BANDS = 1, CW = 2, RW = RW_, NW = NW_, GS = 8;
+  static constexpr bool PAIRS = true;
+  static constexpr int FMA = 0;
   __device__ static Wd e2(Wd a, Wd b) { return OP == DILATE ? max(a, b) : min(a, b); }
+  __device__ static Wd e2h(Wd a, Wd b) { return e2(a, b); }
+  __device__ static Wd e2m(Wd a, Wd b) { return e2(a, b); }
   __device__ static Wd ext3(Wd a, Wd b, Wd c) { return e2(e2(a, b), c); }
   __device__ static Wd ext3h(Wd a, Wd b, Wd c) { return ext3(a, b, c); }
   __device__ static Wd clamp(Wd v, Wd m) { return OP == DILATE ? min(v, m) : max(v, m); }
@@ -420,14 +478,35 @@ struct RR {
     }
   }
 
+  // 2-extreme of one group of the column pass: on the FMA pipe if the
+  // policy's FMA mask has the group's bit (only the u8 policy has that form)
+  template <int GROUP>
+  __device__ static Wd e2g(Wd a, Wd b) {
+    if constexpr ((P::FMA & GROUP) != 0) return P::e2m(a, b);
+    else return P::e2(a, b);
+  }
+
   // row 3-extreme of one word row; the lane-edge neighbours come by shuffle
+  template <bool PAIRED>
   __device__ static void hrow(const Wd (&row)[CW], Wd (&h)[CW]) {
     const Wd left = __shfl_up_sync(0xffffffffu, row[CW - 1], 1);
     const Wd right = __shfl_down_sync(0xffffffffu, row[0], 1);
-    h[0] = P::ext3h(left, row[0], row[1]);
+    if constexpr (PAIRED) {
+      // Without a one-instruction 3-extreme, the 2-extreme of columns
+      // (2i, 2i+1) serves both outputs 2i and 2i+1: 1.5 ops per column.
+      static_assert(CW % 2 == 0, "column pairs");
 #pragma unroll
-    for (int c = 1; c < CW - 1; ++c) h[c] = P::ext3h(row[c - 1], row[c], row[c + 1]);
-    h[CW - 1] = P::ext3h(row[CW - 2], row[CW - 1], right);
+      for (int c = 0; c < CW; c += 2) {
+        const Wd p = P::e2h(row[c], row[c + 1]);
+        h[c] = P::e2h(c == 0 ? left : row[c - 1], p);
+        h[c + 1] = P::e2h(p, c + 2 == CW ? right : row[c + 2]);
+      }
+    } else {
+      h[0] = P::ext3h(left, row[0], row[1]);
+#pragma unroll
+      for (int c = 1; c < CW - 1; ++c) h[c] = P::ext3h(row[c - 1], row[c], row[c + 1]);
+      h[CW - 1] = P::ext3h(row[CW - 2], row[CW - 1], right);
+    }
   }
 
   // One elementary step, in place, on the lane's words. The band's boundary
@@ -457,24 +536,34 @@ struct RR {
     const Wd *dn_slot = xb + (size_t)(warp + 2) * 2 * RWID + lane * CW;
     Wd h[RW][CW];
     if constexpr (CONN == 8) {
-      hrow(w[0], h[0]);
-      hrow(w[RW - 1], h[RW - 1]);
+      hrow<false>(w[0], h[0]);
+      hrow<false>(w[RW - 1], h[RW - 1]);
       *reinterpret_cast<uint4 *>(mine) = P::pack(h[0]);
       *reinterpret_cast<uint4 *>(mine + RWID) = P::pack(h[RW - 1]);
       mbar_arrive(bar);
 #pragma unroll
-      for (int r = 1; r < RW - 1; ++r) hrow(w[r], h[r]);
+      for (int r = 1; r < RW - 1; ++r) hrow<false>(w[r], h[r]);
       Wd pre0[CW], preL[CW];
 #pragma unroll
       for (int c = 0; c < CW; ++c) {
-        pre0[c] = P::e2(h[0][c], h[1][c]);
-        preL[c] = P::e2(h[RW - 2][c], h[RW - 1][c]);
+        pre0[c] = e2g<8>(h[0][c], h[1][c]);
+        preL[c] = e2g<8>(h[RW - 2][c], h[RW - 1][c]);
       }
 #pragma unroll
       for (int r = 1; r < RW - 1; ++r)
 #pragma unroll
         for (int c = 0; c < CW; ++c) {
-          const Wd nv = P::apply(P::ext3(h[r - 1][c], h[r][c], h[r + 1][c]), m[r][c], w[r][c]);
+          Wd v;
+          if constexpr (P::PAIRS && (GEO_RR_PAIRS & 2)) {
+            // the same sharing down the column: pair (2i, 2i+1) of h rows
+            // (pre0 for i = 0, preL for the last pair)
+            static_assert(RW % 2 == 0, "row pairs");
+            v = (r & 1) ? e2g<4>(r == 1 ? pre0[c] : e2g<8>(h[r - 1][c], h[r][c]), h[r + 1][c])
+                        : e2g<4>(h[r - 1][c], r == RW - 2 ? preL[c] : e2g<8>(h[r][c], h[r + 1][c]));
+          } else {
+            v = P::ext3(h[r - 1][c], h[r][c], h[r + 1][c]);
+          }
+          const Wd nv = P::apply(v, m[r][c], w[r][c]);
           obs(r, c, w[r][c], nv);
           w[r][c] = nv;
         }
@@ -487,8 +576,8 @@ struct RR {
         // row 3-extremes of the rows just above / below the band halves
         const Wd hu = P::up(ha[c], h[RW - 1][c]);
         const Wd hd = P::down(h[0][c], hb[c]);
-        const Wd n0 = P::apply(P::e2(pre0[c], hu), m[0][c], w[0][c]);
-        const Wd nL = P::apply(P::e2(preL[c], hd), m[RW - 1][c], w[RW - 1][c]);
+        const Wd n0 = P::apply(e2g<2>(pre0[c], hu), m[0][c], w[0][c]);
+        const Wd nL = P::apply(e2g<2>(preL[c], hd), m[RW - 1][c], w[RW - 1][c]);
         obs(0, c, w[0][c], n0);
         obs(RW - 1, c, w[RW - 1][c], nL);
         w[0][c] = n0;
@@ -501,7 +590,7 @@ struct RR {
       mbar_arrive(bar);
       Wd first[CW], last[CW], pre0[CW], preL[CW];
 #pragma unroll
-      for (int r = 0; r < RW; ++r) hrow(w[r], h[r]);
+      for (int r = 0; r < RW; ++r) hrow<P::PAIRS && (GEO_RR_PAIRS & 1)>(w[r], h[r]);
 #pragma unroll
       for (int c = 0; c < CW; ++c) {
         first[c] = w[0][c];
