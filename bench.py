@@ -177,13 +177,26 @@ def whole_job_rate(world, units_per_rank_step, steps, seconds):
     return world * units_per_rank_step * steps / seconds / 1e9
 
 
-def alu_peak_top_s(nsm, mhz):
+def alu_peak_top_s(nsm, lanes_per_clk, mhz):
     """Peak exact min/max rate for uint8 pixels, in tera pixel-ops per second.
 
-    The fastest exact primitive for uint8 values on sm_103a is max.u16x2 /
-    min.u16x2: 128 lanes per clock per SM, each lane deciding two pixels.
+    The fastest exact primitives for uint8 values on sm_103a are the packed
+    max / min of two u16 lanes (max.u16x2, max.f16x2), each lane deciding one
+    pixel of two. lanes_per_clk is their measured rate per SM clock (the
+    library's probe: 64, half the issue rate of 128).
     """
-    return nsm * 128 * 2 * mhz * 1e6 / 1e12
+    return nsm * lanes_per_clk * 2 * mhz * 1e6 / 1e12
+
+
+def probe_alu(gm):
+    """Lane-ops per SM clock of the faster packed min/max form, and the clock
+    the probe ran at."""
+    best = (0.0, 0.0, "")
+    for form in ("u16x2", "f16x2"):
+        rate, mhz = gm.probe_minmax_rate(form)
+        if rate > best[0]:
+            best = (rate, mhz, form)
+    return best
 
 
 # --- the oracle on the host cores: one process per core (spawned, so it is
@@ -491,6 +504,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    alu_rate, alu_mhz, alu_form = probe_alu(gm)  # roofline denominator, before the warm-up
     for _ in range(args.warmup):
         gm.dilate_chain(marker, mask, args.chain_steps, conn=CONN, out=out)
     torch.cuda.synchronize(dev)
@@ -546,7 +560,8 @@ def main():
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
-    peak = alu_peak_top_s(nsm, sm_max)
+    peak = alu_peak_top_s(nsm, alu_rate, sm_max)
+    issue_peak = alu_peak_top_s(nsm, 128, sm_max)
     per_launch_s = statistics.mean(per) / 1e3
     achieved = px_steps * OPS_PER_PX_STEP / per_launch_s / 1e12
     line = {
@@ -567,8 +582,10 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tpixel-op/s",
                      "frac": achieved / peak, "traffic": measured_traffic(),
                      "traffic_unit": "bytes per launch (dram read + write, ncu)",
-                     "peak_basis": f"{nsm} SMs x 128 lanes/clk x 2 px (max.u16x2) x {sm_max:.0f} MHz",
-                     "ops_per_pixel_step": OPS_PER_PX_STEP},
+                     "peak_basis": f"{nsm} SMs x {alu_rate:.1f} lane-ops/clk (max.{alu_form}, measured by "
+                                   f"geo_probe_minmax_rate at {alu_mhz:.0f} MHz) x 2 px x {sm_max:.0f} MHz",
+                     "ops_per_pixel_step": OPS_PER_PX_STEP,
+                     "issue_rate_peak": issue_peak, "frac_of_issue_rate_peak": achieved / issue_peak},
     }
     if not args.no_secondary and world == 1:
         line.update(secondary(dev))

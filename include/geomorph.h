@@ -345,6 +345,19 @@ GEO_API int geo_dilate_chain_noalloc(geo_dtype dtype, const void *marker, const 
                              int64_t height, int64_t width, int64_t pitch, int conn,
                              int64_t steps, void *stream);
 
+/*
+ * Measurement helper (not part of the method): the rate of the packed
+ * min/max the uint8 step is built from (form 0: max.u16x2, form 1:
+ * max.f16x2), for the ALU roofline of the benchmark. One block of 1024
+ * threads per SM runs 16 independent chains of the instruction per thread;
+ * lane_ops_per_clock receives the lane operations retired per SM clock
+ * (averaged over the SMs, each SM timed by its own clock counter) and
+ * clock_mhz the SM clock over the same span. Synchronous: returns after the
+ * probe on `stream` has finished. GEO_ERR_ARG for another form or a NULL
+ * output, GEO_ERR_CUDA if a launch, the small allocation or the copy fails.
+ */
+GEO_API int geo_probe_minmax_rate(int form, double *lane_ops_per_clock, double *clock_mhz, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

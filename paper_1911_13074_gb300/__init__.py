@@ -27,7 +27,8 @@ __all__ = [
     "GeoError", "load", "library_path", "dilate_chain", "erode_chain", "reconstruct",
     "window_dilate", "window_erode", "device_status", "DTYPES", "geodesic_chain",
     "chain_fwd_ckpt", "chain_backward", "Batch", "OPS", "autotune", "tune_load", "tune_lookup", "plan_info",
-    "hmax", "dome", "hfill", "raobj", "open_rec",
+    "hmax", "dome", "hfill", "raobj", "open_rec", "qdt", "opening", "closing", "asf", "granulometry",
+    "probe_minmax_rate",
 ]
 
 GEO_U8, GEO_F32, GEO_F64 = 0, 1, 2
@@ -131,6 +132,9 @@ def load():
         IPtr = ctypes.POINTER(I)
         lib.geo_plan_info.argtypes = [I, I, I, L, L, L, IPtr, IPtr, IPtr]
         lib.geo_plan_info.restype = I
+        DPtr = ctypes.POINTER(ctypes.c_double)
+        lib.geo_probe_minmax_rate.argtypes = [I, DPtr, DPtr, P]
+        lib.geo_probe_minmax_rate.restype = I
         _lib = lib
         return lib
 
@@ -267,6 +271,20 @@ def device_status(device=None) -> int:
         rc = lib.geo_device_status(torch.cuda.current_stream(dev).cuda_stream, ctypes.byref(v))
     _check(rc, "geo_device_status")
     return int(v.value)
+
+
+def probe_minmax_rate(form: str = "f16x2", device=None):
+    """Measured rate of the packed min/max of the uint8 step (form "u16x2" or
+    "f16x2") on this GPU: (lane-ops per SM clock, SM clock in MHz)."""
+    lib = load()
+    code = {"u16x2": 0, "f16x2": 1}[form]
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    rate, mhz = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    with torch.cuda.device(dev):
+        rc = lib.geo_probe_minmax_rate(code, ctypes.byref(rate), ctypes.byref(mhz),
+                                       torch.cuda.current_stream(dev).cuda_stream)
+    _check(rc, "geo_probe_minmax_rate")
+    return float(rate.value), float(mhz.value)
 
 
 # ---------------------------------------------------------------------------

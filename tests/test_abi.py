@@ -62,6 +62,14 @@ def test_host_argument_checks_need_no_device():
     assert lib.geo_dilate_chain(0, 0x1000, 0x2000, 0x2000, 2, 2, 2, 8, 1, None) == -1
 
 
+def test_probe_rejects_bad_arguments_on_the_host():
+    import paper_1911_13074_gb300 as gm
+    lib = gm.load()
+    r, c = ctypes.c_double(), ctypes.c_double()
+    assert lib.geo_probe_minmax_rate(2, ctypes.byref(r), ctypes.byref(c), None) == -1
+    assert lib.geo_probe_minmax_rate(0, None, ctypes.byref(c), None) == -1
+
+
 def test_tune_cache_file_round_trip(tmp_path):
     """The tune-cache text format loads into the table (no device needed)."""
     import paper_1911_13074_gb300 as gm
