@@ -400,19 +400,32 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
   const size_t ntiles = (size_t)P.tiles_x * (size_t)P.tiles_y * (size_t)batch;
   // [control 256 B][per-tile pass epochs][per-tile changed flags, two passes]
   const size_t ctl_b = 256 + ((3 * ntiles * sizeof(int) + 255) / 256) * 256;
-  const size_t scratch_b = ctl_b + (size_t)spitch_b * (size_t)H * (size_t)batch;
+  int64_t np = 0;
+  if (mode == MODE_CHAIN) {
+    np = rr ? rr_passes(steps, single_tile(P, batch) ? 0 : P.K) : cdiv(steps, P.K);
+    if (alias && (np & 1)) ++np;  // pass 0 must not write the buffer it reads
+  }
+  // uint8 chains of several passes with one tile per CTA hand the passes
+  // over in two zeroed planes of tagged words (GEOMORPH_TAGGED=0: plain
+  // planes and tile epochs); the lane's 4 columns must be whole words
+  const char *tg = getenv("GEOMORPH_TAGGED");
+  const bool tagged = rr && dt == GEO_U8 && mode == MODE_CHAIN && batch == 1 && np >= 2 &&
+                      ntiles <= (size_t)P.grid && P.K % 4 == 0 && P.TW % 4 == 0 && !(tg && strcmp(tg, "0") == 0);
+  const int64_t tpitch = (W + 3) / 4;
+  const size_t tag_b = tagged ? ((2 * (size_t)tpitch * (size_t)H * 8 + 255) / 256) * 256 : 0;
+  const size_t scratch_b = ctl_b + tag_b + (size_t)spitch_b * (size_t)H * (size_t)batch;
   void *scratch = nullptr;
   if (fault == FAULT_ALLOC || cudaMallocFromPoolAsync(&scratch, scratch_b, ds->pool, s) != cudaSuccess)
     return GEO_ERR_CUDA;
   rc = GEO_OK;
-  if (cudaMemsetAsync(scratch, 0, ctl_b, s) != cudaSuccess) rc = GEO_ERR_CUDA;
+  if (cudaMemsetAsync(scratch, 0, ctl_b + tag_b, s) != cudaSuccess) rc = GEO_ERR_CUDA;
 
   TileLaunch L;
   memset(&L, 0, sizeof(L));
   L.marker = make_plane(marker, pitch_b, dt, rr);
   L.mask = make_plane(mask, pitch_b, dt, rr);
   L.out = make_plane(out, pitch_b, dt, rr);
-  L.scratch = make_plane((char *)scratch + ctl_b, spitch_b, dt, rr);
+  L.scratch = make_plane((char *)scratch + ctl_b + tag_b, spitch_b, dt, rr);
   L.marker.bstride = L.out.bstride = H * pitch_b;
   L.mask.bstride = mask ? H * pitch_b : 0;
   L.scratch.bstride = H * spitch_b;
@@ -435,10 +448,11 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
   L.steps_out = steps_out;
   L.fault = fault == FAULT_TIMEOUT ? 1 : 0;
   L.wait_ns = L.fault ? kFaultWaitNs : kWaitLimitNs;
-  if (mode == MODE_CHAIN) {
-    int64_t np = rr ? rr_passes(steps, single_tile(P, batch) ? 0 : P.K) : cdiv(steps, P.K);
-    if (alias && (np & 1)) ++np;  // pass 0 must not write the buffer it reads
-    L.npasses = (int)np;
+  if (mode == MODE_CHAIN) L.npasses = (int)np;
+  if (tagged) {
+    L.tagged = (unsigned long long *)((char *)scratch + ctl_b);
+    L.tpitch = tpitch;
+    L.tplane = tpitch * H;
   }
   if (rc == GEO_OK) rc = rr ? launch_rr(dt, L, op, conn, s, P) : launch_plan(dt, L, op, conn, s, P);
   if (cudaFreeAsync(scratch, s) != cudaSuccess && rc == GEO_OK) rc = GEO_ERR_CUDA;

@@ -82,6 +82,12 @@ struct TileLaunch {
   unsigned long long wait_ns;  // limit of every wait on another CTA
   int fault;              // injected failure (GEOMORPH_FAULT=timeout): the waits on other CTAs
                           // wait for something that never happens, expire and report GEO_ERR_TIMEOUT
+  // register kernel, uint8 chains with one tile per CTA: the passes hand
+  // their results over in two planes of tagged words (4 pixels + the number
+  // of the pass that wrote them) instead of plain planes plus tile epochs;
+  // nullptr: off
+  unsigned long long *tagged;
+  int64_t tpitch, tplane;  // words per row / per plane of `tagged`
 };
 
 // Passes of a chain of `steps` with halo K; K = 0 for a single-tile plan of

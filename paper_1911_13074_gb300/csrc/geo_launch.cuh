@@ -34,15 +34,23 @@ static int occupancy_impl(int op, int conn, size_t smem, int *bps) {
 }
 
 template <template <int> class RP>
-static void *rr_kernel_ptr(int op, int conn) {
-  // RP is one of the single-image policies SU8 / SF32 / SF64
+static void *rr_kernel_ptr(int op, int conn, bool tagged = false) {
+  // RP is one of the single-image policies SU8 / SF32 / SF64; uint8 chains
+  // with tagged planes take the TAG instantiation
+  if constexpr (RR<RP<DILATE>>::kTagged) {
+    if (tagged) {
+      if (op == DILATE)
+        return conn == 8 ? (void *)rr_kernel<RP<DILATE>, 8, true> : (void *)rr_kernel<RP<DILATE>, 4, true>;
+      return conn == 8 ? (void *)rr_kernel<RP<ERODE>, 8, true> : (void *)rr_kernel<RP<ERODE>, 4, true>;
+    }
+  }
   if (op == DILATE) return conn == 8 ? (void *)rr_kernel<RP<DILATE>, 8> : (void *)rr_kernel<RP<DILATE>, 4>;
   return conn == 8 ? (void *)rr_kernel<RP<ERODE>, 8> : (void *)rr_kernel<RP<ERODE>, 4>;
 }
 
 template <template <int> class RP>
 static int launch_rr_impl(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid) {
-  void *k = rr_kernel_ptr<RP>(op, conn);
+  void *k = rr_kernel_ptr<RP>(op, conn, L.tagged != nullptr);
   const size_t smem = rr_smem_bytes<RP<DILATE>>();
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return GEO_ERR_CUDA;

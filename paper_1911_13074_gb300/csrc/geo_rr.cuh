@@ -329,6 +329,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   }
 }
 
+// 64-bit relaxed accesses at gpu scope (single-copy atomic: a tagged word is
+// read whole) and the fence that orders a pass's loads before its stores.
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 // Policies of the single-image kernel (the batch kernel uses the defaults).
 // Taller bands put more work between a warp's arrival and its wait at the
 // step barrier; the host planner (rr_geom in geo_api.cu) mirrors these.
@@ -669,6 +681,97 @@ struct RR {
     }
     return changed;
   }
+
+  // Tagged hand-over between the passes of a uint8 chain (TileLaunch::tagged).
+  // A tagged word holds one lane's CW = 4 pixels of one row in its low 32
+  // bits and, in its high 32 bits, the number of passes completed when it
+  // was written; the planes are zeroed before the launch. Word and tag are
+  // one 64-bit access, so a reader that sees the tag it wants sees the
+  // pixels written with it: the data is its own ready flag, and no release
+  // fence, epoch flag or second round trip stands between a pass's stores
+  // and the next pass's loads of the neighbouring tiles.
+  static constexpr bool kTagged = (B == 2 && CW == 4 && sizeof(G) == 1);
+
+  // Store the interior words of the lane with tag `tag`. The lane's columns
+  // are whole words: K and TW are multiples of 4, so gx is. Cells past the
+  // right image border hold the identity and are stored with their word.
+  __device__ static void store_tagged(const Wd (&w)[RW][CW], unsigned long long *T, int64_t tpitch, int64_t H,
+                                      int64_t W, int64_t ty0, int64_t tx0, int K, int TH, int TW, unsigned tag,
+                                      int lane, int warp) {
+    static_assert(kTagged, "tagged planes hold uint8 pixels");
+    const int X = lane * CW;
+    if (X < K || X + CW > K + TW) return;
+    const int64_t gx = tx0 + (X - K);
+    if (gx >= W) return;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+#pragma unroll
+      for (int r = 0; r < RW; ++r) {
+        const int Y = warp * PH + b * RW + r;
+        if (Y < K || Y >= K + TH) continue;
+        const int64_t gy = ty0 + (Y - K);
+        if (gy >= H) continue;
+        uint32_t px = 0;
+#pragma unroll
+        for (int c = 0; c < CW; ++c) px |= (P::get(w[r][c], b) & 0xffu) << (8 * c);
+        st_relaxed_u64(T + gy * tpitch + (gx >> 2), ((unsigned long long)tag << 32) | px);
+      }
+    }
+  }
+
+  // Load the lane's region rows from the tagged plane T, waiting (bounded)
+  // until every word inside the image carries `tag`. Rows and columns
+  // outside the image take the identity. False if the wait expired.
+  __device__ static bool load_tagged(const unsigned long long *T, int64_t tpitch, int64_t H, int64_t W, int64_t gy0,
+                                     int64_t gx, unsigned tag, unsigned long long limit_ns, Wd (&w)[RW][CW]) {
+    static_assert(kTagged, "tagged planes hold uint8 pixels");
+    constexpr int NR = B * RW;
+    const bool cols = gx >= 0 && gx < W;
+    const unsigned long long *col = T + (cols ? (gx >> 2) : 0);
+    unsigned long long raw[NR];
+    unsigned in = 0;
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+      const int64_t gy = gy0 + i;
+      raw[i] = 0;
+      if (cols && gy >= 0 && gy < H) {
+        raw[i] = ld_relaxed_u64(col + gy * tpitch);
+        in |= 1u << i;
+      }
+    }
+    bool ok = true;
+    unsigned n = 0;
+    unsigned long long t0 = 0;
+    for (;;) {
+      unsigned miss = 0;
+#pragma unroll
+      for (int i = 0; i < NR; ++i)
+        if (((in >> i) & 1u) && (unsigned)(raw[i] >> 32) != tag) miss |= 1u << i;
+      if (!miss) break;
+      if (n == 0) t0 = globaltimer_ns();
+      if ((++n & 15u) == 0 && globaltimer_ns() - t0 > limit_ns) {
+        ok = false;
+        break;
+      }
+#pragma unroll
+      for (int i = 0; i < NR; ++i)
+        if ((miss >> i) & 1u) raw[i] = ld_relaxed_u64(col + (gy0 + i) * tpitch);
+    }
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+      Px lo[CW], hi[CW];
+      P::unpack_raw((uint32_t)raw[r], lo);
+      P::unpack_raw((uint32_t)raw[RW + r], hi);
+#pragma unroll
+      for (int c = 0; c < CW; ++c) {
+        const bool cin = gx + c < W;
+        if (!((in >> r) & 1u) || !cin) lo[c] = P::ident();
+        if (!((in >> (RW + r)) & 1u) || !cin) hi[c] = P::ident();
+        w[r][c] = P::make(lo[c], hi[c]);
+      }
+    }
+    return ok;
+  }
 };
 
 // Wait until every tile of the 3x3 tile neighbourhood of (ty, tx) has
@@ -717,9 +820,13 @@ constexpr size_t rr_smem_bytes() {
   return sizeof(typename P::Wd) * 2 * (P::NW + 2) * 2 * 32 * P::CW;
 }
 
-template <class P, int CONN>
+// TAG: the variant whose chains hand the passes over in tagged planes
+// (uint8, one tile per CTA; TileLaunch::tagged). A separate instantiation,
+// so that the plain kernel's code is not touched by it.
+template <class P, int CONN, bool TAG = false>
 __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
   using R = RR<P>;
+  static_assert(!TAG || R::kTagged, "tagged planes hold uint8 pixels");
   using Wd = typename P::Wd;
   constexpr int CW = R::CW, RW = R::RW, NW = R::NW, PH = R::PH, RWID = R::RWID;
   // boundary-row exchange buffer [parity][warp slot][top/bottom][column], in
@@ -735,6 +842,8 @@ __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
   const bool rec = (L.mode == MODE_REC);
   const bool virt = (L.mask.ptr == nullptr);
   const bool mask_resident = (ntiles <= (int)gridDim.x);
+  // tagged hand-over between chain passes (one tile per CTA, uint8)
+  const bool tagged = TAG && !rec && L.tagged != nullptr && mask_resident;
 
   __shared__ __align__(8) uint64_t xbar;  // split-phase step barrier of the whole CTA
   if (threadIdx.x == 0) mbar_init(&xbar, NW * 32);
@@ -774,7 +883,7 @@ __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
       const int64_t ty0 = (int64_t)ty * TH, tx0 = (int64_t)tx * TW;
       const int64_t gy0 = ty0 - K + warp * PH;
       const int64_t gx = tx0 - K + lane * CW;
-      if (!rec && pass > 0) {
+      if (!rec && pass > 0 && !tagged) {
         // chains synchronise point to point: the tiles whose interiors this
         // tile's halo reads must have finished the previous pass (which also
         // means they are done reading the buffer this pass overwrites)
@@ -803,21 +912,52 @@ __global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
           steps_here = 0;
         }
       }
-      R::load_words(src, L.H, L.W, gy0, gx, src_cg, false, w);
+      bool loaded = false;
+      if constexpr (TAG) {
+        if (tagged && pass > 0) {
+          // the previous pass's words: from this tile's own threads (its
+          // interior) and from the 8 neighbouring tiles (the halo)
+          const unsigned want = L.fault ? (unsigned)pass + (1u << 28) : (unsigned)pass;
+          if (!R::load_tagged(L.tagged + (size_t)((pass - 1) & 1) * L.tplane, L.tpitch, L.H, L.W, gy0, gx, want,
+                              L.wait_ns, w))
+            record_status(L.status, GEO_ERR_TIMEOUT);
+          loaded = true;
+        }
+      }
+      if (!loaded) R::load_words(src, L.H, L.W, gy0, gx, src_cg, false, w);
       if (!mask_resident || pass == 0) R::load_words(mask, L.H, L.W, gy0, gx, false, virt, m);
+      if constexpr (TAG) {
+        // Tagged hand-over: this fence, after the pass's loads and before the
+        // first step's barrier arrival, orders every load of the pass before
+        // every store the CTA makes at its end, and the loads of the
+        // neighbours (which this pass observed through their tags, their own
+        // fences preceding their stores) before this tile's stores too; no
+        // tile overwrites a word of a plane (or, in place, of the marker)
+        // that a neighbour has yet to read.
+        if (tagged) fence_acq_rel_gpu();
+      }
       bool ok = true;
       for (int j = 0; j < steps_here; ++j) {
         ok &= R::template step<CONN>(w, m, &xbuf[parity][0][0][0], &xbar, parity, lane, warp);
         parity ^= 1;
       }
       if (!ok) record_status(L.status, GEO_ERR_TIMEOUT);
-      const bool tile_changed = R::store(w, dst, src, rec, L.H, L.W, ty0, tx0, K, TH, TW, lane, warp);
+      bool stored = false;
+      if constexpr (TAG) {
+        if (tagged && pass + 1 < L.npasses) {
+          R::store_tagged(w, L.tagged + (size_t)(pass & 1) * L.tplane, L.tpitch, L.H, L.W, ty0, tx0, K, TH, TW,
+                          (unsigned)(pass + 1), lane, warp);
+          stored = true;
+        }
+      }
+      const bool tile_changed =
+          stored ? false : R::store(w, dst, src, rec, L.H, L.W, ty0, tx0, K, TH, TW, lane, warp);
       changed |= tile_changed;
       if (rec) {
         const int any = __syncthreads_or(tile_changed ? 1 : 0);
         if (threadIdx.x == 0) L.tchg[(size_t)(pass & 1) * ntiles + t] = any;
       }
-      if (!rec && pass + 1 < L.npasses) {
+      if (!rec && pass + 1 < L.npasses && !tagged) {
         // every thread's stores of this tile happen before the barrier, and
         // the barrier before thread 0's release store, so the release (which
         // is cumulative) publishes the whole tile at gpu scope

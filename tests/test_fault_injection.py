@@ -5,9 +5,10 @@ failure on the host.
             (runs without a GPU);
 * alloc   — the scratch allocation fails: the call returns GEO_ERR_CUDA and
             the Python wrapper raises;
-* timeout — the launch runs, but every wait on another CTA (neighbour epochs
-            of a chain pass, the grid barrier of reconstruction) waits for
-            something that never happens, expires after 20 ms and records
+* timeout — the launch runs, but every wait on another CTA (the tagged words
+            or neighbour epochs of a chain pass, the grid barrier of
+            reconstruction) waits for something that never happens, expires
+            after 20 ms and records
             GEO_ERR_TIMEOUT in the device status word; the kernel returns and
             the context stays usable (the next call is correct).
 """
@@ -62,11 +63,13 @@ def test_alloc_failure_raises():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("kernel", ["rr", "tile"])
+@pytest.mark.parametrize("kernel", ["rr", "rr-plain", "tile"])
 def test_timeout_is_reported_and_the_context_stays_usable(kernel, monkeypatch):
     import torch
     if kernel == "tile":
         monkeypatch.setenv("GEOMORPH_KERNEL", "tile")
+    if kernel == "rr-plain":
+        monkeypatch.setenv("GEOMORPH_TAGGED", "0")
     m = gm()
     w = synth.workload0(300, 300)
     f, g = torch.from_numpy(w["marker"]).cuda(), torch.from_numpy(w["mask"]).cuda()

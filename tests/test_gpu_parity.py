@@ -25,20 +25,19 @@ def gm():
     return m
 
 
-@pytest.fixture(params=["rr", "tile"])
-def kernel(request):
-    """Run a test on the register-resident kernel (default) and on the
+@pytest.fixture(params=["rr", "rr-plain", "tile"])
+def kernel(request, monkeypatch):
+    """Run a test on the register-resident kernel (default: uint8 chains of
+    one tile per CTA hand passes over in tagged planes), on the same kernel
+    with plain planes and tile epochs (GEOMORPH_TAGGED=0), and on the
     shared-memory tile kernel (GEOMORPH_KERNEL=tile)."""
-    old = os.environ.get("GEOMORPH_KERNEL")
+    monkeypatch.delenv("GEOMORPH_KERNEL", raising=False)
+    monkeypatch.delenv("GEOMORPH_TAGGED", raising=False)
     if request.param == "tile":
-        os.environ["GEOMORPH_KERNEL"] = "tile"
-    else:
-        os.environ.pop("GEOMORPH_KERNEL", None)
+        monkeypatch.setenv("GEOMORPH_KERNEL", "tile")
+    elif request.param == "rr-plain":
+        monkeypatch.setenv("GEOMORPH_TAGGED", "0")
     yield request.param
-    if old is None:
-        os.environ.pop("GEOMORPH_KERNEL", None)
-    else:
-        os.environ["GEOMORPH_KERNEL"] = old
 
 
 def dev(a):
