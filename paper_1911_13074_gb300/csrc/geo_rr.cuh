@@ -5,7 +5,9 @@
 // in the shared-memory tile kernel (geo_tile.cuh); what differs is where the
 // tile lives during the K steps: in registers. Chain passes synchronise
 // point to point (a tile waits for the 8 tiles its halo reads to publish the
-// previous pass); reconstruction passes meet at a grid barrier, test a
+// previous pass: uint8 chains through tagged words that carry the pass that
+// wrote them, the others through per-tile epochs); reconstruction passes
+// meet at a grid barrier, test a
 // per-pass "changed" flag, and skip tiles whose 3x3 tile neighbourhood did
 // not change in the previous pass.
 //
