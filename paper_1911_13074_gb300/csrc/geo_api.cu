@@ -407,9 +407,10 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
   }
   // uint8 chains of several passes with one tile per CTA hand the passes
   // over in two zeroed planes of tagged words (GEOMORPH_TAGGED=0: plain
-  // planes and tile epochs); the lane's 4 columns must be whole words
+  // planes and tile epochs); the lane's 4 columns must be whole words. From
+  // 3 passes on: zeroing the planes costs about as much as one hand-over saves.
   const char *tg = getenv("GEOMORPH_TAGGED");
-  const bool tagged = rr && dt == GEO_U8 && mode == MODE_CHAIN && batch == 1 && np >= 2 &&
+  const bool tagged = rr && dt == GEO_U8 && mode == MODE_CHAIN && batch == 1 && np >= kTaggedMinPasses &&
                       ntiles <= (size_t)P.grid && P.K % 4 == 0 && P.TW % 4 == 0 && !(tg && strcmp(tg, "0") == 0);
   const int64_t tpitch = (W + 3) / 4;
   const size_t tag_b = tagged ? ((2 * (size_t)tpitch * (size_t)H * 8 + 255) / 256) * 256 : 0;

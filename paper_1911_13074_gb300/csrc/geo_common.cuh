@@ -98,6 +98,11 @@ struct TileLaunch {
 // at all. A chain then runs in one pass (split only so that a pass's step
 // count fits an int) and reconstruction tests for change every
 // kSoloRecSteps steps.
+// Fewest passes of a uint8 chain or program for the tagged hand-over: the
+// planes are zeroed before the launch (about 2 us at 1024^2), which one
+// hand-over does not repay (1024^2 opening of 2 passes: 25 us plain, 27 us
+// tagged; 1500-step chain of 75 passes: 0.760 -> 0.725 ms).
+constexpr int kTaggedMinPasses = 3;
 constexpr int64_t kSoloPassSteps = (int64_t)1 << 30;
 constexpr int kSoloRecSteps = 64;
 __host__ __device__ inline int64_t rr_passes(int64_t steps, int K) {

@@ -41,26 +41,47 @@ struct Program {
   int64_t steps[kMaxRuns];
 };
 
-template <class P>
+// One pass of one tile. TAG: the uint8 form whose passes hand over in the
+// tagged planes of TileLaunch::tagged (as the chains of rr_kernel do): tin
+// (else the plain src) is read waiting for tag `want`, tout (else the plain
+// dst) is written with tag want + 1.
+template <class P, bool TAG>
 __device__ __forceinline__ bool prog_tile(const TileLaunch &L, const Plane &src, const Plane &dst, bool src_cg,
+                                          const unsigned long long *tin, unsigned long long *tout, unsigned want,
                                           int64_t ty0, int64_t tx0, int S, typename P::Wd *xb0, int xb_stride,
                                           uint64_t *bar, int &parity, int lane, int warp,
                                           typename P::Wd (&w)[P::RW][P::CW], typename P::Wd (&m)[P::RW][P::CW]) {
   using R = RR<P>;
   const int K = L.K;
   const int64_t gy0 = ty0 - K + warp * R::PH, gx = tx0 - K + lane * R::CW;
-  R::load_words(src, L.H, L.W, gy0, gx, src_cg, false, w);
+  bool ok = true, loaded = false;
+  if constexpr (TAG) {
+    if (tin) {
+      ok = R::load_tagged(tin, L.tpitch, L.H, L.W, gy0, gx, L.fault ? want + (1u << 28) : want, L.wait_ns, w);
+      loaded = true;
+    }
+  }
+  if (!loaded) R::load_words(src, L.H, L.W, gy0, gx, src_cg, false, w);
   R::load_words(src, L.H, L.W, gy0, gx, false, true, m);  // the virtual mask of this operation
-  bool ok = true;
+  // tagged hand-over: the loads of the pass before any store of the CTA
+  // (the same write-after-read argument as in rr_kernel)
+  if constexpr (TAG) fence_acq_rel_gpu();
   for (int j = 0; j < S; ++j) {
     ok &= R::template step<8>(w, m, xb0 + (size_t)parity * xb_stride, bar, parity, lane, warp);
     parity ^= 1;
   }
-  R::store(w, dst, src, false, L.H, L.W, ty0, tx0, K, L.TH, L.TW, lane, warp);
+  bool stored = false;
+  if constexpr (TAG) {
+    if (tout) {
+      R::store_tagged(w, tout, L.tpitch, L.H, L.W, ty0, tx0, K, L.TH, L.TW, want + 1, lane, warp);
+      stored = true;
+    }
+  }
+  if (!stored) R::store(w, dst, src, false, L.H, L.W, ty0, tx0, K, L.TH, L.TW, lane, warp);
   return ok;
 }
 
-template <template <int> class RP>
+template <template <int> class RP, bool TAG = false>
 __global__ void __launch_bounds__(RP<DILATE>::NW * 32, 1) prog_kernel(const TileLaunch L, const Program G) {
   using PD = RP<DILATE>;
   using PE = RP<ERODE>;
@@ -96,9 +117,14 @@ __global__ void __launch_bounds__(RP<DILATE>::NW * 32, 1) prog_kernel(const Tile
       const Plane dst = to_out ? L.out : L.scratch;
       const Plane src = p == 0 ? L.marker : (to_out ? L.scratch : L.out);
       const bool src_cg = p > 0 || L.marker.ptr == L.out.ptr;
+      // tagged hand-over (TAG, one tile per CTA): read the previous pass's
+      // plane, write this pass's; no epochs
+      const bool tagged = TAG && L.tagged != nullptr && ntiles <= (int)gridDim.x;
+      const unsigned long long *tin = tagged && p > 0 ? L.tagged + (size_t)((p - 1) & 1) * L.tplane : nullptr;
+      unsigned long long *tout = tagged && p + 1 < G.total_passes ? L.tagged + (size_t)(p & 1) * L.tplane : nullptr;
       for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int ty = t / L.tiles_x, tx = t - ty * L.tiles_x;
-        if (p > 0) {
+        if (p > 0 && !tagged) {
           if (warp == 0 &&
               !wait_neighbours(L.epoch, ty, tx, L.tiles_y, L.tiles_x, L.fault ? p + (1 << 28) : p, lane,
                                L.wait_ns) &&
@@ -107,12 +133,13 @@ __global__ void __launch_bounds__(RP<DILATE>::NW * 32, 1) prog_kernel(const Tile
           __syncthreads();
         }
         const int64_t ty0 = (int64_t)ty * L.TH, tx0 = (int64_t)tx * L.TW;
-        const bool ok = op == DILATE ? prog_tile<PD>(L, src, dst, src_cg, ty0, tx0, S, &xbuf[0][0][0][0],
-                                                     (NW + 2) * 2 * RWID, &xbar, parity, lane, warp, w, m)
-                                     : prog_tile<PE>(L, src, dst, src_cg, ty0, tx0, S, &xbuf[0][0][0][0],
-                                                     (NW + 2) * 2 * RWID, &xbar, parity, lane, warp, w, m);
+        const bool ok =
+            op == DILATE ? prog_tile<PD, TAG>(L, src, dst, src_cg, tin, tout, (unsigned)p, ty0, tx0, S,
+                                              &xbuf[0][0][0][0], (NW + 2) * 2 * RWID, &xbar, parity, lane, warp, w, m)
+                         : prog_tile<PE, TAG>(L, src, dst, src_cg, tin, tout, (unsigned)p, ty0, tx0, S,
+                                              &xbuf[0][0][0][0], (NW + 2) * 2 * RWID, &xbar, parity, lane, warp, w, m);
         if (!ok) record_status(L.status, GEO_ERR_TIMEOUT);
-        if (p + 1 < G.total_passes) {
+        if (p + 1 < G.total_passes && !tagged) {
           __syncthreads();
           if (threadIdx.x == 0) st_release_u32(reinterpret_cast<unsigned *>(L.epoch) + t, (unsigned)(p + 1));
         }
@@ -121,9 +148,9 @@ __global__ void __launch_bounds__(RP<DILATE>::NW * 32, 1) prog_kernel(const Tile
   }
 }
 
-template <template <int> class RP>
+template <template <int> class RP, bool TAG = false>
 int launch_prog(const TileLaunch &L, const Program &G, int grid, cudaStream_t s) {
-  void *k = (void *)prog_kernel<RP>;
+  void *k = (void *)prog_kernel<RP, TAG>;
   const size_t smem = rr_smem_bytes<RP<DILATE>>();
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return GEO_ERR_CUDA;
@@ -161,8 +188,16 @@ int run_program(int dt, const void *f, void *out, int64_t H, int64_t W, int64_t 
   const int64_t spitch_b = ((W * es + 15) / 16) * 16;
   const size_t ntiles = (size_t)P.tiles_x * P.tiles_y;
   const size_t ctl_b = 256 + ((ntiles * sizeof(int) + 255) / 256) * 256;
+  // uint8 programs with one tile per CTA hand the passes over in two planes
+  // of tagged words (as the uint8 chains do; GEOMORPH_TAGGED=0: off), zeroed
+  // before each launch together with the control words
+  const char *tg = getenv("GEOMORPH_TAGGED");
+  const bool tagged = dt == GEO_U8 && ntiles <= (size_t)P.grid && !single_tile(P, 1) && P.K % 4 == 0 &&
+                      P.TW % 4 == 0 && !(tg && strcmp(tg, "0") == 0);
+  const int64_t tpitch = (W + 3) / 4;
+  const size_t tag_b = tagged ? ((2 * (size_t)tpitch * (size_t)H * 8 + 255) / 256) * 256 : 0;
   void *scratch = nullptr;
-  rc = pool_alloc(&scratch, ctl_b + (size_t)spitch_b * H, s);
+  rc = pool_alloc(&scratch, ctl_b + tag_b + (size_t)spitch_b * H, s);
   if (rc != GEO_OK) return rc;
   const void *src = f;
   for (int r0 = 0; r0 < nruns && rc == GEO_OK; r0 += kMaxRuns) {
@@ -188,7 +223,7 @@ int run_program(int dt, const void *f, void *out, int64_t H, int64_t W, int64_t 
       ++G.npasses[G.nruns - 1];
       ++G.total_passes;
     }
-    if (cudaMemsetAsync(scratch, 0, ctl_b, s) != cudaSuccess) {
+    if (cudaMemsetAsync(scratch, 0, ctl_b + tag_b, s) != cudaSuccess) {
       rc = GEO_ERR_CUDA;
       break;
     }
@@ -197,7 +232,7 @@ int run_program(int dt, const void *f, void *out, int64_t H, int64_t W, int64_t 
     L.marker = prog_plane(src, pitch * es, va);
     L.mask = prog_plane(nullptr, 0, 1);
     L.out = prog_plane(out, pitch * es, va);
-    L.scratch = prog_plane((char *)scratch + ctl_b, spitch_b, va);
+    L.scratch = prog_plane((char *)scratch + ctl_b + tag_b, spitch_b, va);
     L.H = H;
     L.W = W;
     L.TH = P.TH;
@@ -211,7 +246,12 @@ int run_program(int dt, const void *f, void *out, int64_t H, int64_t W, int64_t 
     L.ctl = (Control *)scratch;
     L.status = status;
     L.wait_ns = kWaitLimitNs;
-    rc = dt == GEO_U8 ? launch_prog<SU8>(L, G, P.grid, s)
+    if (tagged && G.total_passes >= kTaggedMinPasses) {
+      L.tagged = (unsigned long long *)((char *)scratch + ctl_b);
+      L.tpitch = tpitch;
+      L.tplane = tpitch * H;
+    }
+    rc = dt == GEO_U8 ? (L.tagged ? launch_prog<SU8, true>(L, G, P.grid, s) : launch_prog<SU8>(L, G, P.grid, s))
          : dt == GEO_F32 ? launch_prog<SF32>(L, G, P.grid, s)
                          : launch_prog<SF64>(L, G, P.grid, s);
     src = out;

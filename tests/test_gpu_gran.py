@@ -39,9 +39,14 @@ def host(t):
     return t.cpu().numpy()
 
 
-@pytest.mark.parametrize("kind", ["u8", "f32", "f64"])
+@pytest.mark.parametrize("kind", ["u8", "u8-plain", "f32", "f64"])
 @pytest.mark.parametrize("H,W", SIZES)
-def test_opening_closing_asf_match_oracle(H, W, kind):
+def test_opening_closing_asf_match_oracle(H, W, kind, monkeypatch):
+    """uint8 programs of several tiles hand their passes over in tagged
+    planes; "u8-plain" runs the same with plain planes and tile epochs."""
+    if kind == "u8-plain":
+        monkeypatch.setenv("GEOMORPH_TAGGED", "0")
+        kind = "u8"
     m = gm()
     f = img(H, W, kind)
     fd = torch.from_numpy(f).cuda()

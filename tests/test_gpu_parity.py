@@ -199,6 +199,27 @@ def test_random_shape_sweep():
     assert m.device_status() == 0
 
 
+@pytest.mark.parametrize("H,W", [(300, 300), (129, 1000), (333, 517), (1024, 1024)])
+def test_u8_tagged_hand_over(H, W):
+    """uint8 chains of 3 and more passes with one tile per CTA hand the
+    passes over in tagged planes: multi-tile shapes (a width not a multiple
+    of 4 included), both ops and connectivities, 45 and 101 steps, in place."""
+    m = gm()
+    w = synth.workload0(H, W)
+    f, msk = w["marker"], w["mask"]
+    e = np.minimum(f.astype(np.int32) + 60, 255).astype(np.uint8)
+    for conn in (4, 8):
+        for steps in (45, 101):
+            assert_same(host(m.dilate_chain(dev(f), dev(msk), steps, conn=conn)),
+                        oracle.chain(f, msk, steps, conn=conn), f"dilate {H}x{W} conn{conn} {steps}")
+            assert_same(host(m.erode_chain(dev(e), dev(msk), steps, conn=conn)),
+                        oracle.chain(e, msk, steps, conn=conn, op="erode"), f"erode {H}x{W} conn{conn} {steps}")
+            x = dev(f)
+            m.dilate_chain(x, dev(msk), steps, conn=conn, out=x)
+            assert_same(host(x), oracle.chain(f, msk, steps, conn=conn), f"in place {H}x{W} conn{conn} {steps}")
+    assert m.device_status() == 0
+
+
 @pytest.mark.parametrize("path", ["ranks", "keys"])
 @pytest.mark.parametrize("op", ["dilate", "erode"])
 def test_f64_rank_and_key_paths(path, op, monkeypatch):
