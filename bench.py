@@ -331,10 +331,10 @@ def part_batched(dev):
             op = it["op"]
             if op in (0, 1):
                 (gm.dilate_chain if op == 0 else gm.erode_chain)(it["marker"], it["mask"], it["steps"],
-                                                                conn=it["conn"], out=out)
+                                                                conn=it["conn"], out=out, check=False)
             else:
                 gm.reconstruct(it["marker"], it["mask"], conn=it["conn"], op="dilate" if op == 2 else "erode",
-                               out=out)
+                               out=out, check=False)
     t_plain = _time(plain, 3)
     chain_px_steps = sum(int(it["marker"].numel()) * it["steps"] for it in items if it["op"] in (0, 1))
     res["batched"] = {
@@ -360,14 +360,14 @@ def part_fwd_bwd(dev):
     fb = {}
     for C in (16, 32, 64):
         def fwd_bwd(C=C):
-            out, ws = gm.chain_fwd_ckpt(mk, ms, steps, conn=8, ckpt_interval=C)
-            gm.chain_backward(ms, g, ws, steps, conn=8, ckpt_interval=C)
+            out, ws = gm.chain_fwd_ckpt(mk, ms, steps, conn=8, ckpt_interval=C, check=False)
+            gm.chain_backward(ms, g, ws, steps, conn=8, ckpt_interval=C, check=False)
         fb[C] = _time(fwd_bwd, 3)
     out1 = torch.empty_like(mk)
 
     def plain_fwd():
         for b in range(mk.shape[0]):
-            gm.dilate_chain(mk[b], ms[b], steps, conn=8, out=out1[b])
+            gm.dilate_chain(mk[b], ms[b], steps, conn=8, out=out1[b], check=False)
     t_pf = _time(plain_fwd, 3)
     px = mk.numel() * steps
     res["fwd_bwd"] = {
@@ -398,7 +398,7 @@ def part_reconstruct_4096(dev):
             steps_box = {}
 
             def run():
-                _, st = gm.reconstruct(marker, mask, conn=8, out=out, return_steps=True)
+                _, st = gm.reconstruct(marker, mask, conn=8, out=out, return_steps=True, check=False)
                 steps_box["s"] = st
             t = _time(run, 3)
             n = int(steps_box["s"].item())
@@ -420,10 +420,11 @@ def part_operators(dev):
     import synth
     res = {}
     g = torch.from_numpy(synth.workload1_u8()["mask"]).to(dev)
-    ops = {"hmax_h20": lambda: gm.hmax(g, 20), "dome_h20": lambda: gm.dome(g, 20), "hfill": lambda: gm.hfill(g),
-           "raobj": lambda: gm.raobj(g), "open_rec_s15": lambda: gm.open_rec(g, 15),
-           "qdt": lambda: gm.qdt(g), "pattern_spectrum_0_11": lambda: gm.granulometry(g, 11),
-           "asf_11": lambda: gm.asf(g, 11)}
+    ops = {"hmax_h20": lambda: gm.hmax(g, 20, check=False), "dome_h20": lambda: gm.dome(g, 20, check=False),
+           "hfill": lambda: gm.hfill(g, check=False), "raobj": lambda: gm.raobj(g, check=False),
+           "open_rec_s15": lambda: gm.open_rec(g, 15, check=False), "qdt": lambda: gm.qdt(g, check=False),
+           "pattern_spectrum_0_11": lambda: gm.granulometry(g, 11, check=False),
+           "asf_11": lambda: gm.asf(g, 11, check=False)}
     res["operators_1024_u8"] = {"workload": "1024x1024 u8 workload-1 image, 8-connected",
                                 **{k: {"ms": _time(fn, 3) * 1e3} for k, fn in ops.items()}}
     return res
@@ -444,12 +445,12 @@ def part_workload1(dev):
             fn = gm.dilate_chain if op == "dilate" else gm.erode_chain
             for conn in (4, 8):
                 for n in (100, 500, 1500):
-                    t = _time(lambda: fn(mk, mask, n, conn=conn, out=out), 2)
+                    t = _time(lambda: fn(mk, mask, n, conn=conn, out=out, check=False), 2)
                     res[f"chain_{kind}_{op}_conn{conn}_steps{n}"] = {
                         "ms": t * 1e3, "gpixel_steps_per_s": mask.numel() * n / t / 1e9}
             win = gm.window_dilate if op == "dilate" else gm.window_erode
             for s in (13, 91):
-                t = _time(lambda: win(mask, s, out=out), 2)
+                t = _time(lambda: win(mask, s, out=out, check=False), 2)
                 res[f"window_{kind}_{op}_s{s}"] = {"ms": t * 1e3,
                                                    "gpixel_steps_per_s": mask.numel() * s / t / 1e9}
     return {"workload1_1024": {"workload": "1024x1024 synthetic workload 1 (u8 and f64), every chain and window "
@@ -462,10 +463,15 @@ PARTS = {"batched": part_batched, "fwd_bwd": part_fwd_bwd, "reconstruct_4096": p
 
 def secondary(dev):
     """The batched and forward+backward forms against the plain path, and the
-    other workloads, on the same GPU."""
+    other workloads, on the same GPU. The timed calls are the asynchronous
+    (unchecked) form; the device status word is read after each part."""
+    import paper_1911_13074_gb300 as gm
     res = {}
-    for fn in PARTS.values():
+    for name, fn in PARTS.items():
         res.update(fn(dev))
+        st = gm.device_status()
+        if st != 0:
+            raise RuntimeError(f"device status {st} after the {name} measurements")
     return res
 
 
@@ -506,7 +512,7 @@ def main():
 
     alu_rate, alu_mhz, alu_form = probe_alu(gm)  # roofline denominator, before the warm-up
     for _ in range(args.warmup):
-        gm.dilate_chain(marker, mask, args.chain_steps, conn=CONN, out=out)
+        gm.dilate_chain(marker, mask, args.chain_steps, conn=CONN, out=out, check=False)
     torch.cuda.synchronize(dev)
     if gm.device_status() != 0:
         raise RuntimeError("device status error during warm-up")
@@ -521,7 +527,7 @@ def main():
     for i in range(args.steps):
         flush.fill_(i & 0xFF)
         ev[i][0].record(stream)
-        gm.dilate_chain(marker, mask, args.chain_steps, conn=CONN, out=out)
+        gm.dilate_chain(marker, mask, args.chain_steps, conn=CONN, out=out, check=False)
         ev[i][1].record(stream)
     barrier()
     t_wall = time.perf_counter() - t_wall
@@ -532,7 +538,8 @@ def main():
     if status != 0:
         raise RuntimeError(f"device status {status}")
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers, as a user calls it:
+    # the checked call (it synchronises and reads the device status word)
     out_h = torch.empty_like(marker_h).pin_memory()
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)

@@ -42,7 +42,10 @@
  *   - Errors a call can detect on the host (bad arguments, launch failure)
  *     are returned directly. Errors detected on the device (a bounded wait
  *     that expired, a reconstruction that did not converge) are recorded in
- *     a per-device status word: read it with geo_device_status().
+ *     a per-device status word: read it with geo_device_status(). The word
+ *     keeps the first error until it is read; while it holds one, kernels
+ *     that meet at a grid barrier stop at their next barrier (their output
+ *     is then incomplete), so read it before trusting later results.
  *   - One library instance serves every device; calls use the current device.
  */
 #ifndef GEOMORPH_H
@@ -78,10 +81,12 @@ typedef enum {
 GEO_API const char *geo_status_string(int status);
 
 /*
- * Reads and clears the device status word of the current device after
- * synchronising `stream`. *status receives GEO_OK or the first device-side
+ * Reads and clears the device status words of the current device after
+ * synchronising `stream`: the library's word and the word of
+ * geo_dilate_chain_noalloc. *status receives GEO_OK or the first device-side
  * error (GEO_ERR_TIMEOUT, GEO_ERR_NOT_CONVERGED) recorded since the last
- * read. Returns GEO_ERR_CUDA if the synchronisation itself failed.
+ * read (the library's word first). Allocates nothing. Returns GEO_ERR_CUDA
+ * if the synchronisation or a copy failed.
  */
 GEO_API int geo_device_status(void *stream, int *status);
 
@@ -338,8 +343,12 @@ GEO_API int geo_chain_backward(geo_dtype dtype, int op, const void *mask, const 
  *     corrupt each other's output; the caller must order them.
  *   - The first call on a device sets up that device (looks up the array's
  *     device address and plans the tiles); make it before any stream capture.
- *   - A device-side wait that expires leaves out incomplete; it is not
- *     reported through geo_device_status.
+ *   - Every wait of the kernel on another block is bounded. One that expires
+ *     leaves out incomplete and records GEO_ERR_TIMEOUT in a status word
+ *     inside the static array. The word stays set across later calls until
+ *     geo_device_status reads and clears it (that call allocates nothing on
+ *     a device where only this entry point has run).
+ *   - GEO_ERR_ARG also when the chain needs more than INT_MAX passes.
  */
 GEO_API int geo_dilate_chain_noalloc(geo_dtype dtype, const void *marker, const void *mask, void *out,
                              int64_t height, int64_t width, int64_t pitch, int conn,

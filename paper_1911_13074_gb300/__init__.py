@@ -7,6 +7,14 @@ GeoError on a non-zero status. Every step of the computation runs in the
 library's CUDA kernels; there is no CPU path. If the library is missing it
 is built from csrc/ with nvcc, and if that is impossible the call fails.
 
+Errors found on the device (a bounded wait that expired, a reconstruction
+that reached max_steps) are recorded in a per-device status word. By default
+(check=True) every call synchronises its stream afterwards, reads and clears
+that word, and raises GeoError with the recorded code. check=False keeps the
+call asynchronous (for timing loops and CUDA-graph capture); the caller then
+reads the word with device_status(). The word is sticky: it holds the first
+error recorded since it was last read, by whichever call recorded it.
+
 Operations (Zlaus & Mongus, IEEE TPDS 2019, Section 2):
   dilate_chain / erode_chain   Eq. 3-4, `steps` elementary geodesic steps
   reconstruct                  Eq. 5, iterate until a step changes nothing
@@ -144,6 +152,15 @@ def _check(rc: int, where: str):
         raise GeoError(rc, where)
 
 
+def _finish(device, check: bool, where: str):
+    """With check, synchronise the call's stream and raise the device-side
+    status the call (or an earlier unchecked call) recorded."""
+    if check:
+        v = device_status(device)
+        if v != 0:
+            raise GeoError(v, where + " (device)")
+
+
 _raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
 
 
@@ -194,7 +211,7 @@ def _out_like(marker: torch.Tensor, out):
     return out
 
 
-def _chain(name: str, marker, mask, steps: int, conn: int, out):
+def _chain(name: str, marker, mask, steps: int, conn: int, out, check: bool):
     lib = load()
     _image(marker, "marker")
     _image(mask, "mask")
@@ -205,25 +222,29 @@ def _chain(name: str, marker, mask, steps: int, conn: int, out):
         rc = getattr(lib, name)(DTYPES[marker.dtype], marker.data_ptr(), mask.data_ptr(), out.data_ptr(),
                                 H, W, _pitch(marker), int(conn), int(steps), _stream(marker))
     _check(rc, name)
+    _finish(marker.device, check, name)
     return out
 
 
-def dilate_chain(marker: torch.Tensor, mask: torch.Tensor, steps: int, conn: int = 8, out=None) -> torch.Tensor:
+def dilate_chain(marker: torch.Tensor, mask: torch.Tensor, steps: int, conn: int = 8, out=None,
+                 check: bool = True) -> torch.Tensor:
     """`steps` geodesic dilation steps f <- min(delta_1(f), mask) (Eq. 3-4)."""
-    return _chain("geo_dilate_chain", marker, mask, steps, conn, out)
+    return _chain("geo_dilate_chain", marker, mask, steps, conn, out, check)
 
 
-def erode_chain(marker: torch.Tensor, mask: torch.Tensor, steps: int, conn: int = 8, out=None) -> torch.Tensor:
+def erode_chain(marker: torch.Tensor, mask: torch.Tensor, steps: int, conn: int = 8, out=None,
+                check: bool = True) -> torch.Tensor:
     """`steps` geodesic erosion steps f <- max(eps_1(f), mask) (Eq. 3-4)."""
-    return _chain("geo_erode_chain", marker, mask, steps, conn, out)
+    return _chain("geo_erode_chain", marker, mask, steps, conn, out, check)
 
 
 def reconstruct(marker: torch.Tensor, mask: torch.Tensor, conn: int = 8, op: str = "dilate",
-                max_steps: int = 0, out=None, return_steps: bool = False):
+                max_steps: int = 0, out=None, return_steps: bool = False, check: bool = True):
     """Dilation (op='dilate') or erosion (op='erode') by reconstruction (Eq. 5).
 
-    Device-side non-convergence is recorded in the device status word; call
-    device_status() (it synchronises) to read it.
+    A reconstruction still changing after max_steps records
+    GEO_ERR_NOT_CONVERGED on the device; with check=True it is raised here
+    as GeoError (out then holds the image reached so far).
     """
     lib = load()
     _image(marker, "marker")
@@ -237,10 +258,11 @@ def reconstruct(marker: torch.Tensor, mask: torch.Tensor, conn: int = 8, op: str
                                  H, W, _pitch(marker), int(conn), {"dilate": 0, "erode": 1}[op], int(max_steps),
                                  None if steps is None else steps.data_ptr(), _stream(marker))
     _check(rc, "geo_reconstruct")
+    _finish(marker.device, check, "geo_reconstruct")
     return (out, steps) if return_steps else out
 
 
-def _window(name: str, img, half_size: int, out):
+def _window(name: str, img, half_size: int, out, check: bool):
     lib = load()
     _image(img, "in")
     out = _out_like(img, out)
@@ -249,21 +271,24 @@ def _window(name: str, img, half_size: int, out):
         rc = getattr(lib, name)(DTYPES[img.dtype], img.data_ptr(), out.data_ptr(), H, W, _pitch(img),
                                 int(half_size), _stream(img))
     _check(rc, name)
+    _finish(img.device, check, name)
     return out
 
 
-def window_dilate(img: torch.Tensor, half_size: int, out=None) -> torch.Tensor:
+def window_dilate(img: torch.Tensor, half_size: int, out=None, check: bool = True) -> torch.Tensor:
     """Dilation by the clipped (2s+1)^2 square (Eq. 2), as s unmasked 3x3 steps."""
-    return _window("morph_window_dilate", img, half_size, out)
+    return _window("morph_window_dilate", img, half_size, out, check)
 
 
-def window_erode(img: torch.Tensor, half_size: int, out=None) -> torch.Tensor:
+def window_erode(img: torch.Tensor, half_size: int, out=None, check: bool = True) -> torch.Tensor:
     """Erosion by the clipped (2s+1)^2 square (Eq. 1), as s unmasked 3x3 steps."""
-    return _window("morph_window_erode", img, half_size, out)
+    return _window("morph_window_erode", img, half_size, out, check)
 
 
 def device_status(device=None) -> int:
-    """Synchronise the current stream and read-and-clear the device status word."""
+    """Synchronise the current stream and read-and-clear the device status
+    words (the library's and the no-allocation chain's): 0 or the first
+    device-side error recorded since the last read."""
     lib = load()
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
     with torch.cuda.device(dev):
@@ -306,7 +331,8 @@ def _batch_view(t: torch.Tensor, name: str):
     return t.contiguous()
 
 
-def chain_fwd_ckpt(marker, mask, steps: int, conn: int = 8, op: str = "dilate", ckpt_interval: int = 32):
+def chain_fwd_ckpt(marker, mask, steps: int, conn: int = 8, op: str = "dilate", ckpt_interval: int = 32,
+                   check: bool = True):
     """Forward chain that also stores checkpoints; returns (out, workspace)."""
     lib = load()
     mk = _batch_view(marker, "marker")
@@ -324,11 +350,12 @@ def chain_fwd_ckpt(marker, mask, steps: int, conn: int = 8, op: str = "dilate", 
         rc = lib.geo_chain_fwd_ckpt(dt, _OPS[op], mk.data_ptr(), ms.data_ptr(), out.data_ptr(), H, W, W, int(conn),
                                     int(steps), int(ckpt_interval), B, ws.data_ptr(), int(nbytes), _stream(mk))
     _check(rc, "geo_chain_fwd_ckpt")
+    _finish(mk.device, check, "geo_chain_fwd_ckpt")
     return out.view(marker.shape), ws
 
 
 def chain_backward(mask, grad_out, workspace, steps: int, conn: int = 8, op: str = "dilate",
-                   ckpt_interval: int = 32):
+                   ckpt_interval: int = 32, check: bool = True):
     """(grad_marker, grad_mask) of the chain whose forward wrote `workspace`."""
     lib = load()
     ms = _batch_view(mask, "mask")
@@ -341,6 +368,7 @@ def chain_backward(mask, grad_out, workspace, steps: int, conn: int = 8, op: str
                                     gms.data_ptr(), H, W, W, int(conn), int(steps), int(ckpt_interval), B,
                                     workspace.data_ptr(), _stream(ms))
     _check(rc, "geo_chain_backward")
+    _finish(ms.device, check, "geo_chain_backward")
     return gmk.view(mask.shape), gms.view(mask.shape)
 
 
@@ -438,9 +466,23 @@ class Batch:
         _check(rc, "geo_batch_launch")
         return self.outs
 
-    def run(self):
+    def check(self):
+        """Synchronise and raise if an item recorded a non-zero status (the
+        first such item's code) or the device status word holds an error."""
+        st = self.status[:self.n].cpu()
+        bad = torch.nonzero(st).flatten()
+        if bad.numel():
+            i = int(bad[0])
+            raise GeoError(int(st[i]), f"geo_batch item {i} (device)")
+        _finish(self.device, True, "geo_batch")
+
+    def run(self, check: bool = True):
+        """prepare() and launch(); with check, then check()."""
         self.prepare()
-        return self.launch()
+        outs = self.launch()
+        if check:
+            self.check()
+        return outs
 
 
 # ---------------------------------------------------------------------------
@@ -482,7 +524,7 @@ def plan_info(dtype, op, conn, height, width, steps):
 # geodesic operators (Section 2, Eq. 6-12)
 # ---------------------------------------------------------------------------
 
-def _op(name, f, conn, *extra, out=None):
+def _op(name, f, conn, *extra, out=None, check=True):
     lib = load()
     _image(f, "f")
     out = _out_like(f, out)
@@ -491,39 +533,40 @@ def _op(name, f, conn, *extra, out=None):
         rc = getattr(lib, name)(DTYPES[f.dtype], f.data_ptr(), out.data_ptr(), H, W, _pitch(f), int(conn), *extra,
                                 _stream(f))
     _check(rc, name)
+    _finish(f.device, check, name)
     return out
 
 
-def hmax(f, h, conn=8, out=None):
+def hmax(f, h, conn=8, out=None, check=True):
     """HMAX_h(f) = delta_rec^f(f - h) (Eq. 6)."""
-    return _op("geo_hmax", f, conn, float(h), out=out)
+    return _op("geo_hmax", f, conn, float(h), out=out, check=check)
 
 
-def dome(f, h, conn=8, out=None):
+def dome(f, h, conn=8, out=None, check=True):
     """DOME_h(f) = f - HMAX_h(f) (Eq. 7)."""
-    return _op("geo_dome", f, conn, float(h), out=out)
+    return _op("geo_dome", f, conn, float(h), out=out, check=check)
 
 
-def hfill(f, conn=8, out=None):
+def hfill(f, conn=8, out=None, check=True):
     """HFILL(f): hole filling, erosion by reconstruction from the border (Eq. 8-9)."""
-    return _op("geo_hfill", f, conn, out=out)
+    return _op("geo_hfill", f, conn, out=out, check=check)
 
 
-def raobj(f, conn=8, out=None):
+def raobj(f, conn=8, out=None, check=True):
     """RAOBJ(f): removal of objects touching the border (Eq. 10-11)."""
-    return _op("geo_raobj", f, conn, out=out)
+    return _op("geo_raobj", f, conn, out=out, check=check)
 
 
-def open_rec(f, half_size, conn=8, out=None):
+def open_rec(f, half_size, conn=8, out=None, check=True):
     """gamma_rec^s(f) = delta_rec^f(eps_s(f)), opening by reconstruction (Eq. 12)."""
-    return _op("geo_open_rec", f, conn, int(half_size), out=out)
+    return _op("geo_open_rec", f, conn, int(half_size), out=out, check=check)
 
 
 # ---------------------------------------------------------------------------
 # quasi-distance transform (Section 2, Eq. 13-15; Algorithm 6)
 # ---------------------------------------------------------------------------
 
-def qdt(f, conn=8, lipschitz=True):
+def qdt(f, conn=8, lipschitz=True, check=True):
     """Quasi-distance transform of a uint8 image. Returns (r, d, d_l1): the
     largest residual eps_{j-1}(f) - eps_j(f) over the erosion chain (uint8),
     the first erosion j attaining it (int32, 0 where no erosion lowers the
@@ -541,6 +584,7 @@ def qdt(f, conn=8, lipschitz=True):
         rc = lib.geo_qdt(DTYPES[f.dtype], f.data_ptr(), r.data_ptr(), d.data_ptr(),
                          dl1.data_ptr() if lipschitz else None, H, W, pitch, int(conn), _stream(f))
     _check(rc, "geo_qdt")
+    _finish(f.device, check, "geo_qdt")
     return r, d, dl1
 
 
@@ -548,7 +592,7 @@ def qdt(f, conn=8, lipschitz=True):
 # openings, closings, granulometry, ASF (Section 2, Eq. 16-20)
 # ---------------------------------------------------------------------------
 
-def _win(name, f, s, out):
+def _win(name, f, s, out, check=True):
     lib = load()
     _image(f, "f")
     out = _out_like(f, out)
@@ -556,25 +600,26 @@ def _win(name, f, s, out):
     with _on(f):
         rc = getattr(lib, name)(DTYPES[f.dtype], f.data_ptr(), out.data_ptr(), H, W, _pitch(f), int(s), _stream(f))
     _check(rc, name)
+    _finish(f.device, check, name)
     return out
 
 
-def opening(f, half_size, out=None):
+def opening(f, half_size, out=None, check=True):
     """gamma_s(f) = delta_s(eps_s(f)) with the clipped (2s+1)^2 square (Eq. 16)."""
-    return _win("geo_opening", f, half_size, out)
+    return _win("geo_opening", f, half_size, out, check)
 
 
-def closing(f, half_size, out=None):
+def closing(f, half_size, out=None, check=True):
     """phi_s(f) = eps_s(delta_s(f)) (Eq. 19)."""
-    return _win("geo_closing", f, half_size, out)
+    return _win("geo_closing", f, half_size, out, check)
 
 
-def asf(f, s, out=None):
+def asf(f, s, out=None, check=True):
     """Alternating sequential filter ASF_s(f) = phi_s gamma_s ... phi_1 gamma_1 (f) (Eq. 20)."""
-    return _win("geo_asf", f, s, out)
+    return _win("geo_asf", f, s, out, check)
 
 
-def granulometry(f, smax):
+def granulometry(f, smax, check=True):
     """(G, PS) as float64 CUDA tensors: G_k = sum of gamma_k(f), k = 0..smax
     (Eq. 17), and the pattern spectrum PS_k = G_k - G_{k+1} (Eq. 18)."""
     lib = load()
@@ -586,4 +631,5 @@ def granulometry(f, smax):
         rc = lib.geo_granulometry(DTYPES[f.dtype], f.data_ptr(), H, W, _pitch(f), int(smax), G.data_ptr(),
                                   PS.data_ptr(), _stream(f))
     _check(rc, "geo_granulometry")
+    _finish(f.device, check, "geo_granulometry")
     return G, PS[:int(smax)]

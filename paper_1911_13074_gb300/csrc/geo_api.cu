@@ -2,6 +2,7 @@
 // scratch management, launch. Declarations and contracts: include/geomorph.h.
 #include <cstdio>
 #include <cstdlib>
+#include <climits>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -342,8 +343,7 @@ int run_chain(int dt, const void *marker, const void *mask, void *out, int64_t H
 // launches normally but makes every wait on another CTA (neighbour epochs,
 // grid barrier) wait for something that never happens, so that it expires
 // after kFaultWaitNs and the kernel records GEO_ERR_TIMEOUT and returns.
-enum Fault { FAULT_NONE = 0, FAULT_BADARG, FAULT_ALLOC, FAULT_TIMEOUT };
-static Fault injected_fault() {
+HostFault host_fault() {
   const char *e = getenv("GEOMORPH_FAULT");
   if (!e) return FAULT_NONE;
   if (strcmp(e, "badarg") == 0) return FAULT_BADARG;
@@ -354,7 +354,7 @@ static Fault injected_fault() {
 
 int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64_t H, int64_t W, int64_t pitch,
                   int conn, int op, int mode, int64_t steps, int64_t *steps_out, void *stream, int batch) {
-  const Fault fault = injected_fault();
+  const HostFault fault = host_fault();
   if (fault == FAULT_BADARG) return GEO_ERR_ARG;
   if (batch < 1) return GEO_ERR_ARG;
   if (H < 0 || W < 0 || pitch < W || (conn != 4 && conn != 8) || (op != DILATE && op != ERODE))
@@ -404,6 +404,7 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
   if (mode == MODE_CHAIN) {
     np = rr ? rr_passes(steps, single_tile(P, batch) ? 0 : P.K) : cdiv(steps, P.K);
     if (alias && (np & 1)) ++np;  // pass 0 must not write the buffer it reads
+    if (np > INT_MAX) return GEO_ERR_ARG;  // TileLaunch::npasses is an int
   }
   // uint8 chains of several passes with one tile per CTA hand the passes
   // over in two zeroed planes of tagged words (GEOMORPH_TAGGED=0: plain
@@ -500,14 +501,25 @@ int geo_plan_info(geo_dtype dtype, int op, int conn, int64_t height, int64_t wid
 
 int geo_device_status(void *stream, int *status) {
   if (!status) return GEO_ERR_ARG;
-  DeviceState *ds = nullptr;
-  int rc = device_state(&ds);
-  if (rc != GEO_OK) return rc;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GEO_ERR_CUDA;
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return GEO_ERR_CUDA;
+  // the library's word, if this device has one (no device state is created
+  // here, so a caller of the no-allocation chain allocates nothing by asking)
+  int *word = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_dev[dev].init) word = g_dev[dev].status;
+  }
   int v = 0;
-  if (cudaMemcpy(&v, ds->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GEO_ERR_CUDA;
-  if (cudaMemset(ds->status, 0, sizeof(int)) != cudaSuccess) return GEO_ERR_CUDA;
-  *status = v;
+  if (word) {
+    if (cudaMemcpy(&v, word, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GEO_ERR_CUDA;
+    if (cudaMemset(word, 0, sizeof(int)) != cudaSuccess) return GEO_ERR_CUDA;
+  }
+  // and the no-allocation chain's word
+  int w = 0;
+  if (noalloc_take_status(dev, &w) != GEO_OK) return GEO_ERR_CUDA;
+  *status = v != 0 ? v : w;
   return GEO_OK;
 }
 

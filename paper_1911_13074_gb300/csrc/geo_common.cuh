@@ -128,6 +128,13 @@ int pool_free(void *p, cudaStream_t s);
 
 // The per-device status word that device-side waits report into (geo_api.cu).
 int device_status_word(int **status);
+// Host-side failure injection read from GEOMORPH_FAULT (geo_api.cu).
+enum HostFault { FAULT_NONE = 0, FAULT_BADARG, FAULT_ALLOC, FAULT_TIMEOUT };
+HostFault host_fault();
+// Read and clear the status word of the no-allocation chain on device `dev`
+// (geo_noalloc.cu); 0 if that entry point has not run on the device. The
+// caller has synchronised the stream. Allocates nothing.
+int noalloc_take_status(int dev, int *status);
 
 // Uncached tile planning and launch (geo_api.cu).
 int plan_tiles(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P, int batch = 1);

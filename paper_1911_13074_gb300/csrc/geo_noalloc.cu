@@ -20,7 +20,12 @@
 //     caller must order them;
 //   - the first call on a device looks up the array's device address with
 //     cudaGetSymbolAddress and plans the tiles; make that first call before
-//     any stream capture.
+//     any stream capture;
+//   - a device-side wait that expires (the kernel gives up instead of
+//     hanging, and `out` is then incomplete) is recorded in a status word
+//     inside the array; it stays set across calls until geo_device_status
+//     reads and clears it, which needs no allocation either.
+#include <climits>
 #include <cstring>
 #include <mutex>
 
@@ -31,8 +36,11 @@ namespace geo {
 // Largest scratch image this entry point accepts (16 MiB: a 4096 x 4096
 // uint8 image, a 2048 x 2048 float32 image or a 1448 x 1448 float64 image).
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
-// Control words and the per-call status word, cleared on every call.
+// Header of the array: control words at [0, 128), cleared on every call;
+// the sticky status word at kNoAllocStatusOffset, cleared only when read.
 constexpr size_t kNoAllocHeaderBytes = 512;
+constexpr size_t kNoAllocControlBytes = 128;
+constexpr size_t kNoAllocStatusOffset = 128;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocHeaderBytes + kNoAllocScratchBytes];
 
@@ -107,6 +115,20 @@ int cached_plan(int dev, int dt, int conn, int64_t H, int64_t W, int64_t steps, 
 }
 
 }  // namespace
+
+int noalloc_take_status(int dev, int *status) {
+  *status = 0;
+  char *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (dev >= 0 && dev < kMaxDev && g_na_dev[dev].ready) base = g_na_dev[dev].base;
+  }
+  if (!base) return GEO_OK;  // never ran on this device: nothing recorded
+  int *word = (int *)(base + kNoAllocStatusOffset);
+  if (cudaMemcpy(status, word, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GEO_ERR_CUDA;
+  return cudaMemset(word, 0, sizeof(int)) == cudaSuccess ? GEO_OK : GEO_ERR_CUDA;
+}
+
 }  // namespace geo
 
 using namespace geo;
@@ -115,6 +137,8 @@ extern "C" int geo_dilate_chain_noalloc(geo_dtype dtype, const void *marker, con
                                         int64_t height, int64_t width, int64_t pitch, int conn, int64_t steps,
                                         void *stream) {
   const int dt = (int)dtype;
+  const HostFault fault = host_fault();
+  if (fault == FAULT_BADARG) return GEO_ERR_ARG;
   if (dt != GEO_U8 && dt != GEO_F32 && dt != GEO_F64) return GEO_ERR_DTYPE;
   if (height < 0 || width < 0 || pitch < width || (conn != 4 && conn != 8) || steps < 0) return GEO_ERR_ARG;
   if (height == 0 || width == 0) return GEO_OK;
@@ -150,11 +174,15 @@ extern "C" int geo_dilate_chain_noalloc(geo_dtype dtype, const void *marker, con
     if (rc != GEO_OK) return rc;
   }
 
-  // layout of the static array: [0, 256) control words and this call's
-  // device status word (offset 128), cleared on every call; [512, ...) the
-  // scratch image
+  int64_t np = (steps + P.K - 1) / P.K;
+  if (alias && (np & 1)) ++np;  // pass 0 must not write the buffer it reads
+  if (np > INT_MAX) return GEO_ERR_ARG;  // TileLaunch::npasses is an int
+
+  // layout of the static array: [0, 128) control words, cleared on every
+  // call; the status word at offset 128, sticky until geo_device_status
+  // reads it; [512, ...) the scratch image
   char *ctl = d->base;
-  if (cudaMemsetAsync(ctl, 0, 256, s) != cudaSuccess) return GEO_ERR_CUDA;
+  if (cudaMemsetAsync(ctl, 0, kNoAllocControlBytes, s) != cudaSuccess) return GEO_ERR_CUDA;
 
   TileLaunch L;
   memset(&L, 0, sizeof(L));
@@ -172,12 +200,13 @@ extern "C" int geo_dilate_chain_noalloc(geo_dtype dtype, const void *marker, con
   L.rs = P.rs;
   L.mode = MODE_CHAIN;
   L.steps = steps;
-  L.wait_ns = kWaitLimitNs;
-  int64_t np = (steps + P.K - 1) / P.K;
-  if (alias && (np & 1)) ++np;  // pass 0 must not write the buffer it reads
+  // GEOMORPH_FAULT=timeout: every wait on another CTA waits for something
+  // that never happens and expires after a short limit (host-side injection)
+  L.fault = fault == FAULT_TIMEOUT ? 1 : 0;
+  L.wait_ns = L.fault ? kFaultWaitNs : kWaitLimitNs;
   L.npasses = (int)np;
   L.ctl = (Control *)ctl;
-  L.status = (int *)(d->base + 128);
+  L.status = (int *)(d->base + kNoAllocStatusOffset);
   L.steps_out = nullptr;
   return launch_plan(dt, L, DILATE, conn, s, P);
 }

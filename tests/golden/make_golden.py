@@ -1,10 +1,18 @@
-"""Write tests/golden/workload1_sha256.json: digests of the CPU oracle's
-outputs on the full-size 1024x1024 workload (uint8 and float64; dilation and
-erosion chains of 100, 500 and 1500 steps at 4- and 8-connectivity; square
-windows of half size 13 and 91). Only the oracle runs here; the GPU tests
-compare the SHA-256 of the library's output bytes with these.
+"""Write SHA-256 digests of the CPU oracle's outputs on the full-size
+workloads. Only the oracle runs here; the GPU tests compare the SHA-256 of
+the library's output bytes with these.
 
-    python tests/golden/make_golden.py [--jobs N]
+* set 1 -> workload1_sha256.json: the 1024x1024 workload (uint8 and float64;
+  dilation and erosion chains of 100, 500 and 1500 steps at 4- and
+  8-connectivity; square windows of half size 13 and 91).
+* set 2 -> workload2_sha256.json: the four 4096x4096 reconstructions by
+  dilation to stability (Eq. 5), uint8 and float32 blob masks, with the
+  opening marker (the mask eroded by the 31x31 square, Eq. 1 and Eq. 12) and
+  the h-dome marker (mask - 20, Eq. 6), 8-connected.
+* set 3 -> workload3_sha256.json: every one of the 512 batched items (chains
+  of Eq. 4 or reconstructions of Eq. 5, as drawn per item).
+
+    python tests/golden/make_golden.py [--jobs N] [--sets 1,2,3]
 """
 import argparse
 import hashlib
@@ -15,7 +23,10 @@ import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 sys.path.insert(0, ROOT)
-OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "workload1_sha256.json")
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(HERE, "workload1_sha256.json")
+OUT2 = os.path.join(HERE, "workload2_sha256.json")
+OUT3 = os.path.join(HERE, "workload3_sha256.json")
 LENGTHS = (100, 500, 1500)
 
 
@@ -47,26 +58,85 @@ def window_job(args):
     return {f"window_{kind}_{op}_s{s}": digest(oracle.window(w["mask"], s, op=op))}
 
 
+def rec4096_job(args):
+    kind, marker_kind = args
+    import oracle
+    import synth
+    w = synth.workload2()
+    mask = w["mask_u8"] if kind == "u8" else w["mask_f32"]
+    if marker_kind == "open15":
+        marker = oracle.window(mask, 15, op="erode")
+    else:
+        marker = w["hdome_marker_u8"] if kind == "u8" else w["hdome_marker_f32"]
+    out, n = oracle.reconstruct(marker, mask, conn=8, op="dilate")
+    d = digest(out)
+    d["oracle_changing_steps"] = n
+    res = {f"rec_{kind}_{marker_kind}_conn8": d}
+    if marker_kind == "open15":
+        res[f"window_{kind}_erode_s15"] = digest(marker)
+    return res
+
+
+def item_job(i):
+    import oracle
+    import synth
+    it = synth.workload3()[i]
+    op = it["op"]
+    if op in (synth.OP_DILATE_CHAIN, synth.OP_ERODE_CHAIN):
+        out = oracle.chain(it["marker"], it["mask"], it["steps"], conn=it["conn"],
+                           op="dilate" if op == synth.OP_DILATE_CHAIN else "erode")
+    else:
+        out, _ = oracle.reconstruct(it["marker"], it["mask"], conn=it["conn"],
+                                    op="dilate" if op == synth.OP_DILATE_REC else "erode")
+    return i, digest(out)
+
+
+def write(path, workload, res):
+    with open(path, "w") as fh:
+        json.dump({"generator": "tests/golden/make_golden.py (CPU oracle, oracle/oracle.c)",
+                   "workload": workload, "cases": dict(sorted(res.items()))}, fh, indent=1)
+    print(f"wrote {len(res)} digests to {path}", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--jobs", type=int, default=os.cpu_count() or 4)
+    ap.add_argument("--sets", default="1,2,3")
     a = ap.parse_args()
+    sets = {int(x) for x in a.sets.split(",") if x}
     import oracle
     oracle.build()
-    chains = [(k, o, c) for k in ("u8", "f64") for o in ("dilate", "erode") for c in (4, 8)]
-    wins = [(k, o, s) for k in ("u8", "f64") for o in ("dilate", "erode") for s in (13, 91)]
     ctx = mp.get_context("spawn")
-    res = {}
     with ctx.Pool(a.jobs) as pool:
-        for r in pool.imap_unordered(window_job, wins):
-            res.update(r)
-        for r in pool.imap_unordered(chain_job, chains):
-            res.update(r)
-    with open(OUT, "w") as fh:
-        json.dump({"generator": "tests/golden/make_golden.py (CPU oracle, oracle/oracle.c)",
-                   "workload": "synth.workload1_u8 / workload1_f64, 1024x1024, seed 0x6E0D0001",
-                   "cases": dict(sorted(res.items()))}, fh, indent=1)
-    print(f"wrote {len(res)} digests to {OUT}")
+        if 1 in sets:
+            chains = [(k, o, c) for k in ("u8", "f64") for o in ("dilate", "erode") for c in (4, 8)]
+            wins = [(k, o, s) for k in ("u8", "f64") for o in ("dilate", "erode") for s in (13, 91)]
+            res = {}
+            for r in pool.imap_unordered(window_job, wins):
+                res.update(r)
+            for r in pool.imap_unordered(chain_job, chains):
+                res.update(r)
+            write(OUT, "synth.workload1_u8 / workload1_f64, 1024x1024, seed 0x6E0D0001", res)
+        pending2 = None
+        if 2 in sets:
+            jobs = [(k, mk) for k in ("u8", "f32") for mk in ("open15", "hdome20")]
+            pending2 = pool.map_async(rec4096_job, jobs)
+        if 3 in sets:
+            import synth
+            items = synth.workload3()
+            # largest first, so the long items do not finish last on one core
+            order = sorted(range(len(items)), key=lambda i: -items[i]["marker"].size
+                           * (4 if items[i]["steps"] < 0 else items[i]["steps"] / 500.0))
+            del items
+            res = {}
+            for i, d in pool.imap_unordered(item_job, order):
+                res[f"item{i:03d}"] = d
+            write(OUT3, "synth.workload3, 512 items, seed 0x6E0D0003", res)
+        if pending2 is not None:
+            res = {}
+            for r in pending2.get():
+                res.update(r)
+            write(OUT2, "synth.workload2, 4096x4096, seed 0x6E0D0002", res)
 
 
 if __name__ == "__main__":

@@ -75,10 +75,17 @@ def test_timeout_is_reported_and_the_context_stays_usable(kernel, monkeypatch):
     f, g = torch.from_numpy(w["marker"]).cuda(), torch.from_numpy(w["mask"]).cuda()
     assert m.device_status() == 0
     with fault("timeout"):
-        m.dilate_chain(f, g, 100)  # several passes: the neighbour waits expire
+        m.dilate_chain(f, g, 100, check=False)  # several passes: the neighbour waits expire
         assert m.device_status() == GEO_ERR_TIMEOUT
-        m.reconstruct(f, g)  # the grid barrier expires
+        m.reconstruct(f, g, check=False)  # the grid barrier expires
         assert m.device_status() == GEO_ERR_TIMEOUT
+        # the checked form raises the same code at the call
+        with pytest.raises(m.GeoError) as e:
+            m.dilate_chain(f, g, 100)
+        assert e.value.code == GEO_ERR_TIMEOUT
+        with pytest.raises(m.GeoError) as e:
+            m.reconstruct(f, g)
+        assert e.value.code == GEO_ERR_TIMEOUT
     assert m.device_status() == 0
     np.testing.assert_array_equal(m.dilate_chain(f, g, 100).cpu().numpy(), oracle.chain(w["marker"], w["mask"], 100))
     np.testing.assert_array_equal(m.reconstruct(f, g).cpu().numpy(), oracle.reconstruct(w["marker"], w["mask"])[0])

@@ -28,8 +28,9 @@ def test_chain_and_reconstruction_replay_in_a_graph():
     s.wait_stream(torch.cuda.current_stream())
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
-        m.dilate_chain(mk, ms, 50, out=out_c)
-        m.reconstruct(mk, ms, out=out_r)
+        # no synchronising status read inside a capture: the asynchronous form
+        m.dilate_chain(mk, ms, 50, out=out_c, check=False)
+        m.reconstruct(mk, ms, out=out_r, check=False)
     for w in inputs[1:] + inputs[:1]:
         mk.copy_(torch.from_numpy(w["marker"]))
         ms.copy_(torch.from_numpy(w["mask"]))

@@ -157,11 +157,25 @@ def test_in_place_and_strided(kind, kernel):
 
 
 def test_reconstruct_not_converged_status():
+    """A reconstruction capped below its chain length records
+    GEO_ERR_NOT_CONVERGED on the device (Eq. 5 is not reached): the checked
+    call raises it, the asynchronous call leaves it in the status word."""
     w = synth.workload0(64, 64)
     m = gm()
-    m.reconstruct(dev(w["marker"]), dev(w["mask"]), max_steps=3)
+    with pytest.raises(m.GeoError) as e:
+        m.reconstruct(dev(w["marker"]), dev(w["mask"]), max_steps=3)
+    assert e.value.code == -6
+    assert m.device_status() == 0  # the checked call read and cleared it
+    m.reconstruct(dev(w["marker"]), dev(w["mask"]), max_steps=3, check=False)
     assert m.device_status() == -6
     assert m.device_status() == 0  # read clears
+    # the same through an operator built on reconstruction, and a batch item
+    out = m.reconstruct(dev(w["marker"]), dev(w["mask"]))  # converges: no error
+    np.testing.assert_array_equal(host(out), oracle.reconstruct(w["marker"], w["mask"])[0])
+    b = m.Batch([{"op": "dilate_rec", "marker": dev(w["marker"]), "mask": dev(w["mask"]), "steps": 3}])
+    with pytest.raises(m.GeoError) as e:
+        b.run()
+    assert e.value.code == -6
 
 
 def test_full_size_1024_u8_chain(kernel):
