@@ -243,39 +243,102 @@ class OraclePool:
         self.pool.join()
 
 
+def host_cpu():
+    """(logical cores, CPU model name) of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for ln in fh:
+                    if ln.lower().startswith("model name"):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
+def _omp_task(job):
+    """In a spawned process: the OpenMP build of the oracle (rows of each step
+    split over `threads` threads) runs one chain of `steps` on the workload;
+    returns the wall time. OMP_NUM_THREADS is set before the OpenMP runtime
+    starts (it starts when the library is first loaded in this process)."""
+    steps, threads = job
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    import oracle
+    import synth
+    w = synth.workload1_u8(H, W)
+    oracle.chain_openmp(w["marker_dilate"], w["mask"], 1, conn=CONN)  # load the library, start the threads
+    t0 = time.perf_counter()
+    oracle.chain_openmp(w["marker_dilate"], w["mask"], steps, conn=CONN)
+    return time.perf_counter() - t0
+
+
+class OmpOracle:
+    """One spawned process (safe after this process has used the GPU) running
+    the OpenMP oracle on every host core."""
+
+    def __init__(self, threads=None):
+        import multiprocessing
+        import oracle
+        oracle.build_openmp()  # once, before the worker loads it
+        self.threads = threads or os.cpu_count() or 1
+        self.pool = multiprocessing.get_context("spawn").Pool(1)
+
+    def run(self, steps):
+        return self.pool.apply(_omp_task, ((steps, self.threads),))
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
 def run_reference(args, rank, world):
-    """CPU oracle, timed on the host cores (one process per core) on a bounded
-    sample of the workload: each bench step is one chain of sample_steps per
-    process."""
+    """CPU oracle, timed on the host cores on a bounded sample of the
+    workload: each bench step is sample_steps steps of the chain, run by the
+    OpenMP build of the oracle (the rows of every step split over all host
+    cores: one chain on all cores)."""
     if rank != 0:
         return
-    sample_steps = 20  # chain steps per process and bench step (the full 1500 would take about a minute)
-    pool = OraclePool()
+    sample_steps = 150  # a tenth of the 1500-step chain per bench step
+    nproc, model = host_cpu()
+    omp = OmpOracle(nproc)
     for _ in range(args.warmup):
-        pool.run(sample_steps)
-    dt = sum(pool.run(sample_steps) for _ in range(args.steps))
-    pool.close()
-    value = pool.n * H * W * sample_steps * args.steps / dt / 1e9
-    sample = (f"1024x1024 u8 8-connected dilation chain, {sample_steps} steps in each of {pool.n} processes "
-              f"per bench step")
+        omp.run(sample_steps)
+    dt = sum(omp.run(sample_steps) for _ in range(args.steps))
+    omp.close()
+    value = H * W * sample_steps * args.steps / dt / 1e9
+    sample = (f"1024x1024 u8 8-connected dilation chain, {sample_steps} of the 1500 steps per bench step, "
+              f"one chain with the rows of each step split over {nproc} OpenMP threads ({model})")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Gpixel-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": WORKLOAD, "H": H, "W": W, "chain_steps_timed_per_step": sample_steps,
-                   "processes": pool.n, "conn": CONN},
-        "cpu_baseline": {"value": value, "unit": "Gpixel-steps/s", "cores": pool.n, "kind": "oracle",
-                         "sample": sample},
+                   "threads": nproc, "conn": CONN},
+        "cpu_baseline": {"value": value, "unit": "Gpixel-steps/s", "cores": nproc, "kind": "oracle",
+                         "sample": sample, "cpu_model": model},
         "e2e": {"value": value, "unit": "Gpixel-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def cpu_baseline():
-    """The oracle as it stands on a bounded sample (about 10 s of CPU per
-    process): one process per host core, and the single-core figure."""
+    """The oracle as it stands on bounded samples of the workload (about 8 s
+    each): one chain with the rows of every step split over all host cores
+    (OpenMP), the headline figure; one single-threaded chain per core
+    (independent chains, throughput); and one core."""
     import oracle
     import synth
+    nproc, model = host_cpu()
     w = synth.workload1_u8(H, W)
     f, m = w["marker_dilate"], w["mask"]
     oracle.build()
@@ -289,9 +352,18 @@ def cpu_baseline():
     pool = OraclePool()
     dt = pool.run(n)
     pool.close()
-    return {"value": pool.n * H * W * n / dt / 1e9, "unit": "Gpixel-steps/s", "cores": pool.n, "kind": "oracle",
-            "sample": f"1024x1024 u8 8-connected dilation chain, {n} of the 1500 steps in each of {pool.n} "
-                      f"processes, {dt:.1f} s",
+    omp = OmpOracle(nproc)
+    per_omp = omp.run(5) / 5
+    n_omp = max(5, min(1500, int(8.0 / max(per_omp, 1e-6))))
+    dt_omp = omp.run(n_omp)
+    omp.close()
+    return {"value": H * W * n_omp / dt_omp / 1e9, "unit": "Gpixel-steps/s", "cores": nproc, "kind": "oracle",
+            "sample": f"1024x1024 u8 8-connected dilation chain, {n_omp} of the 1500 steps, one chain with the "
+                      f"rows of each step split over {nproc} OpenMP threads, {dt_omp:.1f} s",
+            "cpu_model": model, "nproc": nproc,
+            "independent_chains": {"value": pool.n * H * W * n / dt / 1e9, "cores": pool.n,
+                                   "sample": f"{n} steps in each of {pool.n} single-threaded processes, "
+                                             f"{dt:.1f} s"},
             "single_core": {"value": H * W * n / dt1 / 1e9, "cores": 1, "seconds": round(dt1, 2)}}
 
 

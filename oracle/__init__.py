@@ -54,6 +54,43 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+_OMP_LIB_PATH = os.path.join(_OUT_DIR, "liboracle_omp.so")
+_omp_lib = None
+
+
+def build_openmp(force: bool = False) -> str:
+    """The same oracle.c compiled with -fopenmp: its step splits the rows of
+    the image over OpenMP threads (OMP_NUM_THREADS), the arithmetic unchanged.
+    Used only for the benchmark's all-core CPU baseline."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_OMP_LIB_PATH)
+            and os.path.getmtime(_OMP_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _OMP_LIB_PATH
+    tmp = _OMP_LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC])
+    os.replace(tmp, _OMP_LIB_PATH)
+    return _OMP_LIB_PATH
+
+
+def chain_openmp(f, m, steps, conn=8, op="dilate"):
+    """oracle.chain through the OpenMP build (one chain on OMP_NUM_THREADS threads)."""
+    global _omp_lib
+    with _lock:
+        if _omp_lib is None:
+            lib = ctypes.CDLL(build_openmp())
+            P, L, I = ctypes.c_void_p, ctypes.c_long, ctypes.c_int
+            lib.oracle_chain.argtypes = [P, P, P, L, L, I, I, L]
+            lib.oracle_chain.restype = I
+            _omp_lib = lib
+    f64 = _f64(f)
+    m64 = None if m is None else _f64(m)
+    out = np.empty_like(f64)
+    H, W = f64.shape
+    if _omp_lib.oracle_chain(_ptr(f64), _ptr(m64), _ptr(out), H, W, conn, _opcode(op), int(steps)) != 0:
+        raise MemoryError("oracle_chain failed")
+    return _back(out, np.asarray(f))
+
+
 def _load():
     global _lib
     with _lock:

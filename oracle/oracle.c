@@ -68,10 +68,14 @@ static double ora_extreme(const double *f, long H, long W, int conn, int op,
 }
 
 /* One elementary geodesic step (Eq. 3 and its dual). m == NULL: no mask
- * (a plain eps_1 / delta_1 step). */
+ * (a plain eps_1 / delta_1 step). Every output pixel depends only on f and
+ * m, so the rows are independent: the build with -fopenmp (the benchmark's
+ * all-core CPU baseline) splits them over threads; the plain build ignores
+ * the pragma. */
 void oracle_step(const double *f, const double *m, double *out, long H, long W,
                  int conn, int op)
 {
+#pragma omp parallel for schedule(static)
     for (long y = 0; y < H; ++y) {
         for (long x = 0; x < W; ++x) {
             double v = ora_extreme(f, H, W, conn, op, y, x, NULL);
