@@ -265,28 +265,45 @@ GEO_API int geo_batch(const geo_item *items, int n, void *workspace, size_t ws_b
               void *stream);
 
 /*
- * Autotuning of the pass length K (which fixes the tile interior), persisted.
- * The paper has no counterpart (its CPU pipeline has no tile size).
- * geo_autotune times every valid K for each item (a geo_item as above; the
- *   call runs the item's operation on its own buffers several times, so out
- *   is overwritten), keeps the fastest per (dtype, op, conn, height, width,
- *   chain-length class) in the library's tune table and, if cache_path is
- *   not NULL, writes the whole table there. Synchronous. GEOMORPH_K must not
- *   be set (GEO_ERR_ARG).
+ * Autotuning of the register kernel's tiles, persisted. The paper has no
+ * counterpart (its CPU pipeline has no tile size). What is searched: the pass
+ * length K (which fixes the tile interior) and the kernel's shape variant
+ * (band height and warps per block, hence the region and the block size):
+ * for uint8, variant 0 = 128x128 pixels / 512 threads, 1 = 128x64 / 256,
+ * 2 = 128x96 / 384; for float32, 0 = 128x128 / 512, 1 = 128x64 / 256 (8-row
+ * bands), 2 = 128x64 / 512 (4-row bands); float64 has variant 0 only.
+ * geo_autotune times every valid (variant, K) for each item (a geo_item as
+ *   above; the call runs the item's operation on its own buffers several
+ *   times, so out is overwritten), keeps the fastest per (dtype, op, conn,
+ *   height, width, chain-length class) and per (dtype, op, conn, size class
+ *   of height, of width, chain-length class) in the library's tune table
+ *   (size classes are half octaves, floor(2 log2 n); a class keeps the
+ *   choice of the largest item tuned in it) and, if cache_path is not NULL,
+ *   writes the whole table there. Each entry also keeps the fastest K of
+ *   variant 0, which the batch kernel (one block size for every item) uses.
+ *   Synchronous. GEOMORPH_K and GEOMORPH_VARIANT must not be set
+ *   (GEO_ERR_ARG).
  * geo_tune_load reads such a file into the tune table (entries from any
  *   device). The environment variable GEOMORPH_TUNE_CACHE names a file that
  *   is loaded on first use, keeping only entries tuned on the same device
  *   model.
- * geo_tune_lookup returns the tuned K for that key, or 0. Chain lengths of 64
- *   and more share one class; reconstruction ignores steps.
+ * geo_tune_reset empties the tune table (the planners' cost models decide
+ *   again; a GEOMORPH_TUNE_CACHE file is not read a second time).
+ * Lookups take the exact (height, width) entry, else its size class.
+ * geo_tune_lookup returns the tuned K of variant 0 for that key, or 0. Chain
+ *   lengths of 64 and more share one class; reconstruction ignores steps.
  * geo_plan_info reports the K and tile interior (TH x TW) the single-image
- *   entry points use for these arguments (op as in geo_item).
+ *   entry points use for these arguments (op as in geo_item);
+ *   geo_plan_shape also the shape variant and the threads per block.
  */
 GEO_API int geo_autotune(const geo_item *items, int n, const char *cache_path);
 GEO_API int geo_tune_load(const char *cache_path);
+GEO_API int geo_tune_reset(void);
 GEO_API int geo_tune_lookup(int dtype, int op, int conn, int64_t height, int64_t width, int64_t steps);
 GEO_API int geo_plan_info(geo_dtype dtype, int op, int conn, int64_t height, int64_t width, int64_t steps,
                   int *K, int *TH, int *TW);
+GEO_API int geo_plan_shape(geo_dtype dtype, int op, int conn, int64_t height, int64_t width, int64_t steps,
+                           int *K, int *TH, int *TW, int *variant, int *threads);
 
 /*
  * Reverse mode of the masked chain (Eq. 4) for GEO_F32 / GEO_F64; the paper

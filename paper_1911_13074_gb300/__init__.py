@@ -34,7 +34,9 @@ from . import build as _build
 __all__ = [
     "GeoError", "load", "library_path", "dilate_chain", "erode_chain", "reconstruct",
     "window_dilate", "window_erode", "device_status", "DTYPES", "geodesic_chain",
-    "chain_fwd_ckpt", "chain_backward", "Batch", "OPS", "autotune", "tune_load", "tune_lookup", "plan_info",
+    "chain_fwd_ckpt", "chain_backward", "Batch", "OPS", "autotune", "tune_load", "tune_reset", "tune_lookup",
+    "plan_info",
+    "plan_shape",
     "hmax", "dome", "hfill", "raobj", "open_rec", "qdt", "opening", "closing", "asf", "granulometry",
     "probe_minmax_rate",
 ]
@@ -119,6 +121,8 @@ def load():
         lib.geo_autotune.restype = I
         lib.geo_tune_load.argtypes = [ctypes.c_char_p]
         lib.geo_tune_load.restype = I
+        lib.geo_tune_reset.argtypes = []
+        lib.geo_tune_reset.restype = I
         lib.geo_tune_lookup.argtypes = [I, I, I, L, L, L]
         lib.geo_tune_lookup.restype = I
         D = ctypes.c_double
@@ -140,6 +144,8 @@ def load():
         IPtr = ctypes.POINTER(I)
         lib.geo_plan_info.argtypes = [I, I, I, L, L, L, IPtr, IPtr, IPtr]
         lib.geo_plan_info.restype = I
+        lib.geo_plan_shape.argtypes = [I, I, I, L, L, L, IPtr, IPtr, IPtr, IPtr, IPtr]
+        lib.geo_plan_shape.restype = I
         DPtr = ctypes.POINTER(ctypes.c_double)
         lib.geo_probe_minmax_rate.argtypes = [I, DPtr, DPtr, P]
         lib.geo_probe_minmax_rate.restype = I
@@ -490,8 +496,9 @@ class Batch:
 # ---------------------------------------------------------------------------
 
 def autotune(items, cache_path=None):
-    """Time every valid pass length K for each item (dicts as for Batch) and
-    keep the fastest in the library's tune table; write it to cache_path."""
+    """Time every valid (shape variant, pass length K) for each item (dicts as
+    for Batch) and keep the fastest per exact size and per size class in the
+    library's tune table; write the table to cache_path."""
     b = Batch(items)  # builds the geo_item array and output buffers
     lib = load()
     with _on(b):
@@ -504,10 +511,25 @@ def tune_load(cache_path):
     _check(load().geo_tune_load(str(cache_path).encode()), "geo_tune_load")
 
 
+def tune_reset():
+    """Empty the library's tune table (the cost models decide again)."""
+    _check(load().geo_tune_reset(), "geo_tune_reset")
+
+
 def tune_lookup(dtype, op, conn, height, width, steps) -> int:
     dt = DTYPES[dtype] if isinstance(dtype, torch.dtype) else int(dtype)
     code = OPS[op] if isinstance(op, str) else int(op)
     return int(load().geo_tune_lookup(dt, code, int(conn), int(height), int(width), int(steps)))
+
+
+def plan_shape(dtype, op, conn, height, width, steps):
+    """(K, TH, TW, variant, threads per block) of the single-image plan."""
+    dt = DTYPES[dtype] if isinstance(dtype, torch.dtype) else int(dtype)
+    code = OPS[op] if isinstance(op, str) else int(op)
+    v = [ctypes.c_int(0) for _ in range(5)]
+    _check(load().geo_plan_shape(dt, code, int(conn), int(height), int(width), int(steps), *[ctypes.byref(x) for x in v]),
+           "geo_plan_shape")
+    return tuple(x.value for x in v)
 
 
 def plan_info(dtype, op, conn, height, width, steps):

@@ -192,17 +192,24 @@ static int make_plan(int dt, int op, int conn, int64_t H, int64_t W, int64_t ste
 struct RRGeom {
   int CW, RW, NW, B;
 };
-// must match SU8 / SF32 / SF64 in geo_rr.cuh (CW, RW, NW, bands)
-static RRGeom rr_geom(int dt) {
+// must match SU8 / SF32 / SF64 and their variants in geo_rr.cuh (CW, RW, NW, bands)
+static RRGeom rr_geom(int dt, int variant = 0) {
+  if (dt == GEO_U8 && variant == 1) return RRGeom{4, GEO_RR_U8_V1_RW, GEO_RR_U8_V1_NW, 2};
+  if (dt == GEO_U8 && variant == 2) return RRGeom{4, GEO_RR_U8_V2_RW, GEO_RR_U8_V2_NW, 2};
   if (dt == GEO_U8 || dt == GEO_D32) return RRGeom{4, GEO_RR_U8_RW, GEO_RR_U8_NW, 2};
+  if (dt == GEO_F32 && variant == 1) return RRGeom{4, GEO_RR_F32_V1_RW, GEO_RR_F32_V1_NW, 1};
+  if (dt == GEO_F32 && variant == 2) return RRGeom{4, GEO_RR_F32_V2_RW, GEO_RR_F32_V2_NW, 1};
   if (dt == GEO_F32) return RRGeom{4, GEO_RR_F32_RW, GEO_RR_F32_NW, 1};
   return RRGeom{2, GEO_RR_F64_RW, GEO_RR_F64_NW, 1};
 }
 
-static int occupancy_rr(int dt, int op, int conn, int *bps) {
-  if (dt == GEO_U8) return occupancy_rr_u8(op, conn, bps);
+// shape variants an element type has (uint8 and float32: kRRVariants)
+static int rr_variants(int dt) { return (dt == GEO_U8 || dt == GEO_F32) ? kRRVariants : 1; }
+
+static int occupancy_rr(int dt, int op, int conn, int *bps, int variant = 0) {
+  if (dt == GEO_U8) return occupancy_rr_u8(op, conn, bps, variant);
   if (dt == GEO_D32) return occupancy_rr_d32(op, conn, bps);
-  if (dt == GEO_F32) return occupancy_rr_f32(op, conn, bps);
+  if (dt == GEO_F32) return occupancy_rr_f32(op, conn, bps, variant);
   return occupancy_rr_f64(op, conn, bps);
 }
 
@@ -211,11 +218,11 @@ static int occupancy_rr(int dt, int op, int conn, int *bps) {
 // kSyncSteps for its load / store / grid barrier, and every step costs one
 // unit per tile an SM has to process in that pass.
 static int plan_rr_uncached(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P,
-                            int batch, int tunedK) {
-  const RRGeom g = rr_geom(dt);
+                            int batch, int tunedK, int variant) {
+  const RRGeom g = rr_geom(dt, variant);
   const int RWID = 32 * g.CW, RHGT = g.NW * g.RW * g.B;
   int bps = 0;
-  if (occupancy_rr(dt, op, conn, &bps) != GEO_OK || bps <= 0) return GEO_ERR_CUDA;
+  if (occupancy_rr(dt, op, conn, &bps, variant) != GEO_OK || bps <= 0) return GEO_ERR_CUDA;
   double kSyncSteps = 10.0;
   if (const char *e = getenv("GEOMORPH_SYNC")) kSyncSteps = atof(e);
   // K fixed by the GEOMORPH_K override, else by the tune cache, else chosen
@@ -231,7 +238,9 @@ static int plan_rr_uncached(int dt, int op, int conn, int64_t H, int64_t W, int6
     if (forceK > 0 && K != ((forceK + g.CW - 1) / g.CW) * g.CW) continue;
     const int TW = RWID - 2 * K, TH = RHGT - 2 * K;
     const int64_t tiles = cdiv(H, TH) * cdiv(W, TW) * batch;
-    const double per_sm = (double)cdiv(tiles, nsm);
+    // blocks resident at once: a step of one region takes one unit of an SM
+    // per resident block (bps > 1 only for the small variants)
+    const double per_sm = (double)cdiv(tiles, (int64_t)nsm * bps) * bps;
     // one tile covering one image runs without pass boundaries (rr_passes)
     const bool one = tiles == 1;
     double cost;
@@ -251,7 +260,7 @@ static int plan_rr_uncached(int dt, int op, int conn, int64_t H, int64_t W, int6
     if (cost < best) {
       best = cost;
       const int64_t slots = (int64_t)bps * nsm;
-      bp = Plan{TH, TW, K, 0, (int)cdiv(W, TW), (int)cdiv(H, TH), (int)(tiles < slots ? tiles : slots), 0};
+      bp = Plan{TH, TW, K, 0, (int)cdiv(W, TW), (int)cdiv(H, TH), (int)(tiles < slots ? tiles : slots), 0, variant};
       (void)batch;
     }
   }
@@ -263,15 +272,31 @@ static int plan_rr_uncached(int dt, int op, int conn, int64_t H, int64_t W, int6
 using RRPlanKey = std::tuple<int, int, int, int, int, int64_t, int64_t, int64_t, int, std::string, std::string, int>;
 static std::map<RRPlanKey, Plan> g_rr_plans;
 
-// code: the operation as a geo_item.op code (0..5), for the tune cache
+// code: the operation as a geo_item.op code (0..5), for the tune cache.
+// variants: whether the plan may use a shape variant of the kernel (the
+// chains, reconstructions and windows of run_chain_any); the other kernels
+// built on the same region (programs, the distance transform) take the
+// default shape and the tuned K of that shape.
 static int make_plan_rr(int dt, int op, int code, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm,
-                        Plan *P, int batch) {
+                        Plan *P, int batch, bool variants = false) {
   int dev = 0;
   cudaGetDevice(&dev);
   const char *ek = getenv("GEOMORPH_K");
   const char *es = getenv("GEOMORPH_SYNC");
-  const int tk = ek ? 0 : tuned_k(dt, code, conn, H, W, steps_hint);
-  RRPlanKey key{dev, batch, dt, op, conn, H, W, steps_hint, nsm, ek ? ek : "", es ? es : "", tk};
+  const char *ev = getenv("GEOMORPH_VARIANT");
+  int tk = 0, tv = 0;
+  if (variants && ev) {
+    // variant override (the autotuner's sweep); K from GEOMORPH_K or the cost model
+    tv = atoi(ev);
+    if (tv < 0 || tv >= rr_variants(dt)) return GEO_ERR_ARG;
+  } else if (!ek) {
+    if (variants && batch == 1) {
+      if (!tuned_plan(dt, code, conn, H, W, steps_hint, &tk, &tv) || tv < 0 || tv >= rr_variants(dt)) tk = tv = 0;
+    } else {
+      tk = tuned_k(dt, code, conn, H, W, steps_hint);
+    }
+  }
+  RRPlanKey key{dev, batch, dt, op, conn, H, W, steps_hint, nsm, ek ? ek : "", es ? es : "", tk * 16 + tv};
   {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     auto it = g_rr_plans.find(key);
@@ -280,11 +305,11 @@ static int make_plan_rr(int dt, int op, int code, int conn, int64_t H, int64_t W
       return GEO_OK;
     }
   }
-  int rc = plan_rr_uncached(dt, op, conn, H, W, steps_hint, nsm, P, batch, tk);
+  int rc = plan_rr_uncached(dt, op, conn, H, W, steps_hint, nsm, P, batch, tk, tv);
   if (rc == GEO_OK && getenv("GEOMORPH_DEBUG"))
-    fprintf(stderr, "geomorph rr plan: dt=%d op=%d conn=%d %lldx%lld steps=%lld -> interior %dx%d K=%d tiles=%dx%d grid=%d\n",
+    fprintf(stderr, "geomorph rr plan: dt=%d op=%d conn=%d %lldx%lld steps=%lld -> interior %dx%d K=%d tiles=%dx%d grid=%d variant=%d\n",
             dt, op, conn, (long long)H, (long long)W, (long long)steps_hint, P->TH, P->TW, P->K, P->tiles_y,
-            P->tiles_x, P->grid);
+            P->tiles_x, P->grid, P->variant);
   if (rc == GEO_OK) {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     g_rr_plans[key] = *P;
@@ -293,9 +318,9 @@ static int make_plan_rr(int dt, int op, int code, int conn, int64_t H, int64_t W
 }
 
 static int launch_rr(int dt, const TileLaunch &L, int op, int conn, cudaStream_t s, const Plan &P) {
-  if (dt == GEO_U8) return launch_rr_u8(L, op, conn, s, P.grid);
+  if (dt == GEO_U8) return launch_rr_u8(L, op, conn, s, P.grid, P.variant);
   if (dt == GEO_D32) return launch_rr_d32(L, op, conn, s, P.grid);
-  if (dt == GEO_F32) return launch_rr_f32(L, op, conn, s, P.grid);
+  if (dt == GEO_F32) return launch_rr_f32(L, op, conn, s, P.grid, P.variant);
   return launch_rr_f64(L, op, conn, s, P.grid);
 }
 
@@ -390,7 +415,7 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
   const bool rr = !(kern && strcmp(kern, "tile") == 0) || dt == GEO_D32;  // the distances have no tile kernel
   Plan P;
   const int code = mode == MODE_REC ? 2 + op : (mask ? op : 4 + op);
-  rc = rr ? make_plan_rr(dt, op, code, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P, batch)
+  rc = rr ? make_plan_rr(dt, op, code, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P, batch, true)
           : make_plan(dt, op, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P, batch);
   if (rc != GEO_OK) return rc;
 
@@ -483,6 +508,11 @@ const char *geo_status_string(int status) {
 
 int geo_plan_info(geo_dtype dtype, int op, int conn, int64_t height, int64_t width, int64_t steps, int *K, int *TH,
                   int *TW) {
+  return geo_plan_shape(dtype, op, conn, height, width, steps, K, TH, TW, nullptr, nullptr);
+}
+
+int geo_plan_shape(geo_dtype dtype, int op, int conn, int64_t height, int64_t width, int64_t steps, int *K, int *TH,
+                   int *TW, int *variant, int *threads) {
   if (dtype != GEO_U8 && dtype != GEO_F32 && dtype != GEO_F64) return GEO_ERR_DTYPE;
   if (op < 0 || op > 5 || height <= 0 || width <= 0 || (op < 4 && conn != 4 && conn != 8)) return GEO_ERR_ARG;
   DeviceState *ds = nullptr;
@@ -491,11 +521,13 @@ int geo_plan_info(geo_dtype dtype, int op, int conn, int64_t height, int64_t wid
   const bool rec = (op == 2 || op == 3);
   const int eop = (op == 1 || op == 3 || op == 5) ? ERODE : DILATE;
   Plan P;
-  rc = make_plan_rr(dtype, eop, op, op >= 4 ? 8 : conn, height, width, rec ? 0 : steps, ds->nsm, &P, 1);
+  rc = make_plan_rr(dtype, eop, op, op >= 4 ? 8 : conn, height, width, rec ? 0 : steps, ds->nsm, &P, 1, true);
   if (rc != GEO_OK) return rc;
   if (K) *K = P.K;
   if (TH) *TH = P.TH;
   if (TW) *TW = P.TW;
+  if (variant) *variant = P.variant;
+  if (threads) *threads = rr_geom(dtype, P.variant).NW * 32;
   return GEO_OK;
 }
 

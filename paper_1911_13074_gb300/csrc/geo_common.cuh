@@ -37,6 +37,21 @@ constexpr unsigned long long kFaultWaitNs = 20000000ULL;    // 20 ms
 #define GEO_RR_F64_NW 16
 #endif
 
+// Pre-built shapes of the register-resident kernel that the autotuner can
+// choose among (variant 0 is the default above). uint8: 128x64 pixels with
+// 8 warps and 128x96 with 12 warps; float32: 128x64 with 8 warps of 8 rows
+// and 128x64 with 16 warps of 4 rows. Smaller regions give an image more
+// tiles, which pays when its tiles alone would leave SMs idle.
+constexpr int kRRVariants = 3;
+#define GEO_RR_U8_V1_RW 4
+#define GEO_RR_U8_V1_NW 8
+#define GEO_RR_U8_V2_RW 4
+#define GEO_RR_U8_V2_NW 12
+#define GEO_RR_F32_V1_RW 8
+#define GEO_RR_F32_V1_NW 8
+#define GEO_RR_F32_V2_RW 4
+#define GEO_RR_F32_V2_NW 16
+
 // One image operand of a pass: base pointer, row stride in bytes, and
 // whether 16-byte vector access is legal (base and stride 16-byte aligned).
 struct Plane {
@@ -115,12 +130,16 @@ __host__ __device__ inline int64_t rr_passes(int64_t steps, int K) {
 struct Plan {
   int TH, TW, K, rs, tiles_x, tiles_y, grid;
   size_t smem;
+  int variant;  // register kernel: shape variant (0 = default)
 };
 inline bool single_tile(const Plan &P, int batch) { return batch <= 1 && P.tiles_x == 1 && P.tiles_y == 1; }
 
-// Tuned pass length K for an item-op code (0..5 as geo_item.op), or 0 when
-// the tune cache has no entry (geo_tune.cu).
+// Tuned pass length K of the default kernel shape for an item-op code (0..5
+// as geo_item.op), or 0 when the tune cache has no entry (geo_tune.cu). The
+// entry of the exact (H, W) is used first, else that of its size class.
 int tuned_k(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps);
+// Tuned (K, variant) over every kernel shape; false when there is no entry.
+bool tuned_plan(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps, int *K, int *variant);
 
 // Stream-ordered scratch from the library's per-device pool (geo_api.cu).
 int pool_alloc(void **p, size_t n, cudaStream_t s);
@@ -162,11 +181,20 @@ int plan_rr(int dt, int op, int code, int conn, int64_t H, int64_t W, int64_t st
 int launch_tile_u8(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid, size_t smem);
 int launch_tile_f32(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid, size_t smem);
 int launch_tile_f64(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid, size_t smem);
-int launch_rr_u8(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid);
-int launch_rr_f32(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid);
+int launch_rr_u8(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid, int variant = 0);
+int launch_rr_f32(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid, int variant = 0);
 int launch_rr_f64(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid);
-int occupancy_rr_u8(int op, int conn, int *blocks_per_sm);
-int occupancy_rr_f32(int op, int conn, int *blocks_per_sm);
+int occupancy_rr_u8(int op, int conn, int *blocks_per_sm, int variant = 0);
+int occupancy_rr_f32(int op, int conn, int *blocks_per_sm, int variant = 0);
+// the variant shapes, one translation unit each (geo_rr_u8_v<n>.cu, geo_rr_f32_v<n>.cu)
+int launch_rr_u8_v1(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid);
+int launch_rr_u8_v2(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid);
+int occupancy_rr_u8_v1(int op, int conn, int *blocks_per_sm);
+int occupancy_rr_u8_v2(int op, int conn, int *blocks_per_sm);
+int launch_rr_f32_v1(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid);
+int launch_rr_f32_v2(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid);
+int occupancy_rr_f32_v1(int op, int conn, int *blocks_per_sm);
+int occupancy_rr_f32_v2(int op, int conn, int *blocks_per_sm);
 int occupancy_rr_f64(int op, int conn, int *blocks_per_sm);
 int launch_rr_d32(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid);
 int occupancy_rr_d32(int op, int conn, int *blocks_per_sm);

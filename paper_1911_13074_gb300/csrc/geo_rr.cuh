@@ -349,6 +349,11 @@ __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_re
 template <int OP> using SU8 = RU8<OP, GEO_RR_U8_RW, GEO_RR_U8_NW>;
 template <int OP> using SF32 = RF32<OP, GEO_RR_F32_RW, GEO_RR_F32_NW>;
 template <int OP> using SF64 = RF64<OP, GEO_RR_F64_RW, GEO_RR_F64_NW>;
+// the autotuner's other shapes (geo_common.cuh)
+template <int OP> using SU8V1 = RU8<OP, GEO_RR_U8_V1_RW, GEO_RR_U8_V1_NW>;
+template <int OP> using SU8V2 = RU8<OP, GEO_RR_U8_V2_RW, GEO_RR_U8_V2_NW>;
+template <int OP> using SF32V1 = RF32<OP, GEO_RR_F32_V1_RW, GEO_RR_F32_V1_NW>;
+template <int OP> using SF32V2 = RF32<OP, GEO_RR_F32_V2_RW, GEO_RR_F32_V2_NW>;
 
 // ---------------------------------------------------------------------------
 // the kernel
@@ -825,8 +830,10 @@ constexpr size_t rr_smem_bytes() {
 // TAG: the variant whose chains hand the passes over in tagged planes
 // (uint8, one tile per CTA; TileLaunch::tagged). A separate instantiation,
 // so that the plain kernel's code is not touched by it.
+// Blocks of 8 warps or fewer (the smaller shape variants) are bounded to
+// 128 registers a thread, so that two of them fit on one SM.
 template <class P, int CONN, bool TAG = false>
-__global__ void __launch_bounds__(P::NW * 32, 1) rr_kernel(const TileLaunch L) {
+__global__ void __launch_bounds__(P::NW * 32, P::NW <= 8 ? 2 : 1) rr_kernel(const TileLaunch L) {
   using R = RR<P>;
   static_assert(!TAG || R::kTagged, "tagged planes hold uint8 pixels");
   using Wd = typename P::Wd;

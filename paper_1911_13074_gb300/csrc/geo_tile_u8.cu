@@ -10,10 +10,16 @@ int launch_tile_u8(const TileLaunch &L, int op, int conn, cudaStream_t s, int gr
 
 int occupancy_tile_u8(int op, int conn, size_t smem, int *bps) { return occupancy_impl<EU8>(op, conn, smem, bps); }
 
-int launch_rr_u8(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid) {
+int launch_rr_u8(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid, int variant) {
+  if (variant == 1) return launch_rr_u8_v1(L, op, conn, s, grid);
+  if (variant == 2) return launch_rr_u8_v2(L, op, conn, s, grid);
   return launch_rr_impl<SU8>(L, op, conn, s, grid);
 }
 
-int occupancy_rr_u8(int op, int conn, int *bps) { return occupancy_rr_impl<SU8>(op, conn, bps); }
+int occupancy_rr_u8(int op, int conn, int *bps, int variant) {
+  if (variant == 1) return occupancy_rr_u8_v1(op, conn, bps);
+  if (variant == 2) return occupancy_rr_u8_v2(op, conn, bps);
+  return occupancy_rr_impl<SU8>(op, conn, bps);
+}
 
 }  // namespace geo

@@ -11,8 +11,14 @@ the library's output bytes with these.
   the h-dome marker (mask - 20, Eq. 6), 8-connected.
 * set 3 -> workload3_sha256.json: every one of the 512 batched items (chains
   of Eq. 4 or reconstructions of Eq. 5, as drawn per item).
+* set 4 -> table5_1024_sha256.json: the operators of the paper's Table 5 on
+  the 1024x1024 uint8 workload image (the mask of set 1), 8-connected:
+  HMAX_20 and DOME_20 (Eq. 6-7), HFILL (Eq. 8-9), RAOBJ (Eq. 10-11), the
+  opening by reconstruction with s = 15 (Eq. 12), and the quasi-distance
+  transform (r and d of Eq. 13 as Algorithm 6 computes them, and the eta
+  limit of Eq. 14-15).
 
-    python tests/golden/make_golden.py [--jobs N] [--sets 1,2,3]
+    python tests/golden/make_golden.py [--jobs N] [--sets 1,2,3,4]
 """
 import argparse
 import hashlib
@@ -27,6 +33,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "workload1_sha256.json")
 OUT2 = os.path.join(HERE, "workload2_sha256.json")
 OUT3 = os.path.join(HERE, "workload3_sha256.json")
+OUT4 = os.path.join(HERE, "table5_1024_sha256.json")
 LENGTHS = (100, 500, 1500)
 
 
@@ -91,6 +98,22 @@ def item_job(i):
     return i, digest(out)
 
 
+def table5_job(name):
+    import numpy as np
+    import oracle
+    import synth
+    g = synth.workload1_u8()["mask"]
+    if name == "qdt":
+        r, d = oracle.qdt_residual(g, conn=8)
+        dl1, _ = oracle.qdt_lipschitz(d, conn=8)
+        return {"qdt_r_conn8": digest(r), "qdt_d_conn8": digest(d.astype(np.int32)),
+                "qdt_dl1_conn8": digest(dl1.astype(np.int32))}
+    fn = {"hmax_h20": lambda: oracle.hmax(g, 20, conn=8), "dome_h20": lambda: oracle.dome(g, 20, conn=8),
+          "hfill": lambda: oracle.hfill(g, conn=8), "raobj": lambda: oracle.raobj(g, conn=8),
+          "open_rec_s15": lambda: oracle.open_rec(g, 15, conn=8)}[name]
+    return {f"{name}_conn8": digest(fn())}
+
+
 def write(path, workload, res):
     with open(path, "w") as fh:
         json.dump({"generator": "tests/golden/make_golden.py (CPU oracle, oracle/oracle.c)",
@@ -117,6 +140,10 @@ def main():
             for r in pool.imap_unordered(chain_job, chains):
                 res.update(r)
             write(OUT, "synth.workload1_u8 / workload1_f64, 1024x1024, seed 0x6E0D0001", res)
+        pending4 = None
+        if 4 in sets:
+            pending4 = pool.map_async(table5_job, ["qdt", "hfill", "raobj", "open_rec_s15", "hmax_h20",
+                                                   "dome_h20"])
         pending2 = None
         if 2 in sets:
             jobs = [(k, mk) for k in ("u8", "f32") for mk in ("open15", "hdome20")]
@@ -132,6 +159,11 @@ def main():
             for i, d in pool.imap_unordered(item_job, order):
                 res[f"item{i:03d}"] = d
             write(OUT3, "synth.workload3, 512 items, seed 0x6E0D0003", res)
+        if pending4 is not None:
+            res = {}
+            for r in pending4.get():
+                res.update(r)
+            write(OUT4, "synth.workload1_u8 mask, 1024x1024 uint8, seed 0x6E0D0001", res)
         if pending2 is not None:
             res = {}
             for r in pending2.get():

@@ -1,17 +1,20 @@
 """GPU parity at the workloads' full sizes, in the launch configuration the
-benchmark uses (the planner's default plan).
+benchmark uses (the planners' default plans; for workload 3 also the
+autotuned plans and the graph-captured batched launch the benchmark times).
+Every output is compared with the SHA-256 of the oracle's output, written by
+tests/golden/make_golden.py (which runs only the oracle):
 
-* 1024x1024 (workload 1): every chain and window case is compared with the
-  SHA-256 of the oracle's output, written by tests/golden/make_golden.py
-  (which runs only the oracle).
-* 4096x4096 (workload 2): reconstruction to stability is too long for the
-  oracle here, so the result is checked through properties that determine it
-  at any size: the opening marker (31x31 erosion) equals the oracle's window,
-  one more oracle step changes nothing (fixed point), marker <= out <= mask,
-  and for sampled levels t the set {out >= t} is exactly the union of the
-  connected components of {mask >= t} that meet delta_1({marker >= t}) --
-  which characterises the least fixed point above the marker (Eq. 5).
-* Workload 3 (512 items): the batched launch equals the single-item calls.
+* 1024x1024 (workload 1): every chain and window case.
+* 4096x4096 (workload 2): the four reconstructions to stability (uint8 and
+  float32 blob masks; the opening marker, the mask eroded by the 31x31
+  square, and the h-dome marker mask - 20), and the opening marker itself.
+  Beside the digests, properties that determine the result at any size are
+  checked too: one more oracle step changes nothing (fixed point),
+  marker <= out <= mask, and for sampled levels t the set {out >= t} is the
+  union of the connected components of {mask >= t} that meet
+  delta_1({marker >= t}) -- the least fixed point above the marker (Eq. 5).
+* Workload 3 (512 items): every item of the batched launch, of the
+  single-item calls and of the batched launch after autotuning.
 """
 import hashlib
 import json
@@ -27,7 +30,10 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "workload1_sha256.json")
+GOLDEN_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+GOLDEN = os.path.join(GOLDEN_DIR, "workload1_sha256.json")
+GOLDEN2 = os.path.join(GOLDEN_DIR, "workload2_sha256.json")
+GOLDEN3 = os.path.join(GOLDEN_DIR, "workload3_sha256.json")
 
 
 def gm():
@@ -84,15 +90,19 @@ def level_set_check(rec, marker, mask, conn, levels):
 def test_workload2_full_size_reconstruction(kind):
     w = synth.workload2()
     m = gm()
+    digests = json.load(open(GOLDEN2))["cases"]
     mask = w["mask_u8"] if kind == "u8" else w["mask_f32"]
     hdome = w["hdome_marker_u8"] if kind == "u8" else w["hdome_marker_f32"]
     md = torch.from_numpy(mask).cuda()
     # (a) opening by reconstruction: marker = mask eroded by the 31x31 square
     ero = m.window_erode(md, 15)
+    assert sha(ero) == digests[f"window_{kind}_erode_s15"]["sha256"], "31x31 erosion differs from the oracle's"
     ero_h = ero.cpu().numpy()
-    np.testing.assert_array_equal(ero_h, oracle.window(mask, 15, op="erode"))
-    for marker in (ero_h, hdome):
+    for name, marker in (("open15", ero_h), ("hdome20", hdome)):
         rec, steps = m.reconstruct(torch.from_numpy(marker).cuda(), md, conn=8, return_steps=True)
+        assert sha(rec) == digests[f"rec_{kind}_{name}_conn8"]["sha256"], f"{name}: differs from the oracle's"
+        # the steps applied cover the oracle's changing steps plus the step that finds no change
+        assert int(steps.item()) >= digests[f"rec_{kind}_{name}_conn8"]["oracle_changing_steps"] + 1
         out = rec.cpu().numpy()
         assert m.device_status() == 0
         assert np.all(marker <= out) and np.all(out <= mask)
@@ -101,33 +111,53 @@ def test_workload2_full_size_reconstruction(kind):
         level_set_check(out, marker, mask, 8, np.unique(levels))
 
 
-def test_workload3_full_batch_equals_single_item_calls():
+def test_workload3_every_item_against_oracle_digests():
+    """The 512 items batched (the prepared launch captured in a CUDA graph and
+    replayed, as the benchmark times it), as 512 single-item calls, and
+    batched again after autotuning the items (shape variant and K per item
+    and size class): every output against its oracle digest."""
     m = gm()
+    digests = json.load(open(GOLDEN3))["cases"]
     items = []
     for it in synth.workload3():
         items.append({"op": it["op"], "marker": torch.from_numpy(it["marker"]).cuda(),
                       "mask": torch.from_numpy(it["mask"]).cuda(),
                       "steps": 0 if it["steps"] < 0 else it["steps"], "conn": it["conn"]})
-    b = m.Batch(items)
-    b.run()
-    torch.cuda.synchronize()
-    assert bool((b.status[:len(items)] == 0).all())
-    for i, it in enumerate(items):
+
+    def batched_graph():
+        b = m.Batch(items).prepare()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            b.launch()
+        torch.cuda.current_stream().wait_stream(s)
+        for o in b.outs:
+            o.fill_(7)  # what the replay writes is what is checked
+        g.replay()
+        b.check()
+        return b.outs
+
+    def compare(outs, what):
+        bad = [i for i, o in enumerate(outs) if sha(o) != digests[f"item{i:03d}"]["sha256"]]
+        assert not bad, f"{what}: items {bad[:10]} differ from the oracle ({len(bad)} of {len(outs)})"
+
+    compare(batched_graph(), "batched (cost-model plans)")
+    singles = []
+    for it in items:
         op = it["op"]
         if op in (0, 1):
-            ref = (m.dilate_chain if op == 0 else m.erode_chain)(it["marker"], it["mask"], it["steps"], conn=it["conn"])
+            singles.append((m.dilate_chain if op == 0 else m.erode_chain)(it["marker"], it["mask"], it["steps"],
+                                                                        conn=it["conn"]))
         else:
-            ref = m.reconstruct(it["marker"], it["mask"], conn=it["conn"], op="dilate" if op == 2 else "erode")
-        assert torch.equal(b.outs[i], ref), f"item {i}"
-    # and a few of the smallest items against the oracle directly
-    sizes = sorted(range(len(items)), key=lambda i: items[i]["marker"].numel())[:6]
-    for i in sizes:
-        it = items[i]
-        f, g = it["marker"].cpu().numpy(), it["mask"].cpu().numpy()
-        op = it["op"]
-        ref = (oracle.chain(f, g, it["steps"], conn=it["conn"], op="dilate" if op == 0 else "erode") if op in (0, 1)
-               else oracle.reconstruct(f, g, conn=it["conn"], op="dilate" if op == 2 else "erode")[0])
-        np.testing.assert_array_equal(b.outs[i].cpu().numpy(), ref)
+            singles.append(m.reconstruct(it["marker"], it["mask"], conn=it["conn"],
+                                         op="dilate" if op == 2 else "erode"))
+    compare(singles, "single-item calls")
+    try:
+        m.autotune(items)
+        compare(batched_graph(), "batched (autotuned plans)")
+    finally:
+        m.tune_reset()
 
 
 def test_chain_and_window_past_32bit_offsets():
