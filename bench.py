@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--only", default=None, choices=["batched", "fwd_bwd", "reconstruct_4096", "operators",
                                                     "workload1"],
                    help="run one secondary measurement alone (for profiler captures) and print it")
+    p.add_argument("--write-traffic-record", nargs=2, metavar=("NCU_CSV", "OUT_JSON"), default=None,
+                   help="write the chain kernel's DRAM traffic record from the CSV of the ncu capture "
+                        "(TRAFFIC_COMMAND) and exit")
     p.add_argument("--chain-steps", type=int, default=CHAIN_STEPS,
                    help="chain length of a bench step (default 1500; shorter only for small profiler captures, "
                         "and then named in the output's config)")
@@ -148,13 +151,54 @@ def measured_traffic():
     """DRAM bytes per launch of the chain kernel from the committed ncu record,
     or None when the kernel sources changed since the counters were taken."""
     try:
-        with open(os.path.join(ROOT, "profiles", "rr_kernel_u8_1024_chain1500_traffic.json")) as fh:
+        with open(TRAFFIC_RECORD) as fh:
             rec = json.load(fh)
     except (OSError, ValueError):
         return None
     if rec.get("source_sha256") != kernel_source_sha256():
         return None
     return rec.get("traffic_bytes_per_launch")
+
+
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "rr_kernel_u8_1024_chain1500_traffic.json")
+TRAFFIC_COMMAND = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                   "--clock-control none --print-units base -k regex:rr_kernel -s 1 -c 1 --csv --log-file <csv> "
+                   "python bench.py --steps 1 --warmup 1 --no-secondary --no-cpu-baseline")
+
+
+def write_traffic_record(csv_path, out_path):
+    """Turn the ncu CSV of TRAFFIC_COMMAND (one captured launch of the timed
+    chain kernel) into the traffic record bench.py reads, stamped with the
+    SHA-256 of the chain kernel's sources as they are when this runs (right
+    after the capture, on the same checkout)."""
+    import csv
+    vals, name = {}, None
+    with open(csv_path, newline="") as fh:
+        rows = [r for r in csv.reader(fh) if r]
+    head = next(i for i, r in enumerate(rows) if "Metric Name" in r)
+    cols = rows[head]
+    for r in rows[head + 1:]:
+        if len(r) != len(cols):
+            continue
+        d = dict(zip(cols, r))
+        name = d.get("Kernel Name", name)
+        vals[d["Metric Name"]] = (float(d["Metric Value"].replace(",", "")), d.get("Metric Unit", ""))
+    rd, wr = vals["dram__bytes_read.sum"], vals["dram__bytes_write.sum"]
+    dur = vals["gpu__time_duration.sum"]
+    for v in (rd, wr):
+        if v[1] not in ("byte", "bytes", ""):
+            raise ValueError(f"unexpected unit {v[1]} (the capture takes --print-units base)")
+    rec = {"kernel": name, "workload": "1024x1024 u8 workload 1, 1500-step chain, one launch (the timed launch "
+                                       "of the command)",
+           "command": TRAFFIC_COMMAND, "passes": 1,
+           "dram_bytes_read": rd[0], "dram_bytes_write": wr[0], "traffic_bytes_per_launch": rd[0] + wr[0],
+           "gpu_time_ms_under_ncu": dur[0] / 1e6 if dur[1].startswith("n") else dur[0],
+           "source_sha256": kernel_source_sha256(),
+           "note": "written by bench.py --write-traffic-record from the capture's CSV; source_sha256 is computed "
+                   "from the chain kernel's sources at that moment"}
+    with open(out_path, "w") as fh:
+        json.dump(rec, fh, indent=1)
+    return rec
 
 
 def max_over_ranks(values, world, device=None):
@@ -430,8 +474,11 @@ def part_batched(dev):
         return t_b, t_p
 
     t_batch_cm, t_plain_cm = measure()
+    # autotuning: the shape and K of every item's single-image calls, then
+    # the batch planner's pass-length policy on the batch itself
     t0 = time.perf_counter()
     gm.autotune(items)
+    gm.Batch(items).autotune()
     tune_s = time.perf_counter() - t0
     t_batch, t_plain = measure()
     res = {"batched": {
@@ -580,6 +627,9 @@ def secondary(dev):
 
 def main():
     args = parse()
+    if args.write_traffic_record:
+        print(json.dumps(write_traffic_record(*args.write_traffic_record)), flush=True)
+        return
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)

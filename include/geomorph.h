@@ -247,7 +247,9 @@ GEO_API size_t geo_batch_workspace_size(const geo_item *items, int n);
 /*
  * geo_batch = geo_batch_prepare + geo_batch_launch.
  * geo_batch_prepare uploads the items' descriptors (tile geometry, K per
- *   item) from host memory into the workspace; stream-ordered.
+ *   item) from host memory into the workspace; stream-ordered. It also sets
+ *   up the library's state on the current device (allocated on first use),
+ *   so that the launch that follows allocates nothing.
  * geo_batch_launch resets the queue and runs every item to completion in one
  *   persistent cooperative kernel; it copies nothing from the host, so a
  *   prepared workspace can be launched repeatedly (and captured in a CUDA
@@ -263,6 +265,22 @@ GEO_API int geo_batch_prepare(const geo_item *items, int n, void *workspace, siz
 GEO_API int geo_batch_launch(const geo_item *items, int n, void *workspace, int *status_out, void *stream);
 GEO_API int geo_batch(const geo_item *items, int n, void *workspace, size_t ws_bytes, int *status_out,
               void *stream);
+
+/*
+ * Autotuning of the batch's tiles (not in the paper). The batch planner gives
+ * each item the pass length K that minimises tile-steps plus a per-pass
+ * charge (the hand-over between passes and the queue), in units of one
+ * region-step; the charge is the tuned policy. geo_batch_autotune prepares
+ * and launches these items with each candidate charge (2.5, 5, 10, 20, 40,
+ * 80), times two launches after a warm-up with CUDA events on `stream`,
+ * keeps the fastest under which every item completed (status_out, if given,
+ * is checked), stores it in the library's tune table (written to cache_path
+ * if not NULL, with the rest of the table) for every later
+ * geo_batch_prepare, and leaves the workspace prepared with it. Synchronous;
+ * the items' outputs are overwritten. Untuned, the charge is 10.
+ */
+GEO_API int geo_batch_autotune(const geo_item *items, int n, void *workspace, size_t ws_bytes, int *status_out,
+                               void *stream, const char *cache_path);
 
 /*
  * Autotuning of the register kernel's tiles, persisted. The paper has no
@@ -289,6 +307,8 @@ GEO_API int geo_batch(const geo_item *items, int n, void *workspace, size_t ws_b
  *   model.
  * geo_tune_reset empties the tune table (the planners' cost models decide
  *   again; a GEOMORPH_TUNE_CACHE file is not read a second time).
+ * geo_tune_save writes the tune table to a file (the format geo_tune_load
+ *   reads).
  * Lookups take the exact (height, width) entry, else its size class.
  * geo_tune_lookup returns the tuned K of variant 0 for that key, or 0. Chain
  *   lengths of 64 and more share one class; reconstruction ignores steps.
@@ -299,6 +319,7 @@ GEO_API int geo_batch(const geo_item *items, int n, void *workspace, size_t ws_b
 GEO_API int geo_autotune(const geo_item *items, int n, const char *cache_path);
 GEO_API int geo_tune_load(const char *cache_path);
 GEO_API int geo_tune_reset(void);
+GEO_API int geo_tune_save(const char *cache_path);
 GEO_API int geo_tune_lookup(int dtype, int op, int conn, int64_t height, int64_t width, int64_t steps);
 GEO_API int geo_plan_info(geo_dtype dtype, int op, int conn, int64_t height, int64_t width, int64_t steps,
                   int *K, int *TH, int *TW);

@@ -34,7 +34,7 @@ from . import build as _build
 __all__ = [
     "GeoError", "load", "library_path", "dilate_chain", "erode_chain", "reconstruct",
     "window_dilate", "window_erode", "device_status", "DTYPES", "geodesic_chain",
-    "chain_fwd_ckpt", "chain_backward", "Batch", "OPS", "autotune", "tune_load", "tune_reset", "tune_lookup",
+    "chain_fwd_ckpt", "chain_backward", "Batch", "OPS", "autotune", "tune_load", "tune_save", "tune_reset", "tune_lookup",
     "plan_info",
     "plan_shape",
     "hmax", "dome", "hfill", "raobj", "open_rec", "qdt", "opening", "closing", "asf", "granulometry",
@@ -117,6 +117,10 @@ def load():
         lib.geo_batch_launch.restype = I
         lib.geo_batch.argtypes = [IP, I, P, ctypes.c_size_t, P, P]
         lib.geo_batch.restype = I
+        lib.geo_batch_autotune.argtypes = [IP, I, P, ctypes.c_size_t, P, P, ctypes.c_char_p]
+        lib.geo_batch_autotune.restype = I
+        lib.geo_tune_save.argtypes = [ctypes.c_char_p]
+        lib.geo_tune_save.restype = I
         lib.geo_autotune.argtypes = [IP, I, ctypes.c_char_p]
         lib.geo_autotune.restype = I
         lib.geo_tune_load.argtypes = [ctypes.c_char_p]
@@ -472,6 +476,18 @@ class Batch:
         _check(rc, "geo_batch_launch")
         return self.outs
 
+    def autotune(self, cache_path=None):
+        """Time these items batched under each candidate pass-length policy,
+        keep the fastest for every later prepare() (and in cache_path), and
+        leave this batch prepared with it. Overwrites the outputs."""
+        lib = load()
+        with _on(self):
+            rc = lib.geo_batch_autotune(self.items, self.n, self.workspace.data_ptr(), self.nbytes,
+                                        self.status.data_ptr(), torch.cuda.current_stream(self.device).cuda_stream,
+                                        None if cache_path is None else str(cache_path).encode())
+        _check(rc, "geo_batch_autotune")
+        return self
+
     def check(self):
         """Synchronise and raise if an item recorded a non-zero status (the
         first such item's code) or the device status word holds an error."""
@@ -509,6 +525,11 @@ def autotune(items, cache_path=None):
 
 def tune_load(cache_path):
     _check(load().geo_tune_load(str(cache_path).encode()), "geo_tune_load")
+
+
+def tune_save(cache_path):
+    """Write the library's tune table to a file."""
+    _check(load().geo_tune_save(str(cache_path).encode()), "geo_tune_save")
 
 
 def tune_reset():

@@ -151,8 +151,18 @@ __device__ void fill_identity_slots(const BItem &it, char *xb) {
 
 }  // namespace
 
-__global__ void batch_init(BatchArgs A, const int *order, unsigned long long ntasks0) {
-  // states, status, queue slots, and the pass-0 tasks in `order`
+__global__ void batch_init(BatchArgs A, const int *order) {
+  // states, status, queue slots, and the pass-0 tasks in `order`; the
+  // pass-0 task count comes from the uploaded item table (whatever policy
+  // prepared it)
+  __shared__ unsigned long long ntasks0_s;
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int i = 0; i < A.n; ++i) t += (unsigned long long)A.items[i].tiles_x * (unsigned long long)A.items[i].tiles_y;
+    ntasks0_s = t;
+  }
+  __syncthreads();
+  const unsigned long long ntasks0 = ntasks0_s;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
     BState s;
     s.pass = 0;
@@ -322,11 +332,18 @@ bool is_rec(const geo_item &x) { return x.op == 2 || x.op == 3; }
 bool is_win(const geo_item &x) { return x.op == 4 || x.op == 5; }
 bool is_empty(const geo_item &x) { return x.height == 0 || x.width == 0; }
 
+// Candidate per-pass charges of the batch planner's cost model (the policy
+// geo_batch_autotune chooses among; 10 is the untuned default).
+constexpr double kBatchSyncs[] = {2.5, 5.0, 10.0, 20.0, 40.0, 80.0};
+constexpr int kNumBatchSyncs = sizeof(kBatchSyncs) / sizeof(kBatchSyncs[0]);
+
 // K for one item: the register-resident region of its element type with the
-// halo chosen by the single-image cost model (item tiles run concurrently
-// with other items' tiles, so the cost counts tile-steps plus a per-pass
-// synchronisation charge). GEOMORPH_BATCH_K overrides it for tuning.
-int item_k(const geo_item &x) {
+// halo chosen by a cost model for tiles that run concurrently with other
+// items' tiles: tile-steps plus `sync` region-steps per pass (the pass
+// hand-over and the queue). The single-image tune entries are not used
+// here: they favour many tiles, which a batch does not need (it gets its
+// parallelism from the other items). GEOMORPH_BATCH_K overrides K.
+int item_k(const geo_item &x, double sync) {
   const RRG g = rrg(x.dtype);
   const int RWID = 32 * g.CW, RHGT = g.NW * g.RW * g.B;
   const int kmax = (RWID < RHGT ? RWID : RHGT) / 2 - g.CW;
@@ -334,13 +351,7 @@ int item_k(const geo_item &x) {
     int k = ((atoi(e) + g.CW - 1) / g.CW) * g.CW;
     if (k >= g.CW && k <= kmax) return k;
   }
-  {
-    // a measured K for this item shape (geo_autotune) takes precedence
-    const int tk = tuned_k(x.dtype, x.op, is_win(x) ? 8 : x.conn, x.height, x.width, x.steps);
-    if (tk >= g.CW && tk <= kmax && tk % g.CW == 0) return tk;
-  }
   const bool rec = is_rec(x);
-  const double sync = 10.0;
   double best = 1e300;
   int bk = g.CW;
   const double n = rec ? (double)(x.height > x.width ? x.height : x.width) : (double)(x.steps > 0 ? x.steps : 1);
@@ -383,11 +394,11 @@ struct Geometry {
   int K, TH, TW, tiles_x, tiles_y;
 };
 
-Geometry item_geometry(const geo_item &x) {
+Geometry item_geometry(const geo_item &x, double sync) {
   Geometry g{};
   if (is_empty(x)) return g;
   const RRG r = rrg(x.dtype);
-  g.K = item_k(x);
+  g.K = item_k(x, sync);
   g.TW = 32 * r.CW - 2 * g.K;
   g.TH = r.NW * r.RW * r.B - 2 * g.K;
   g.tiles_x = (int)((x.width + g.TW - 1) / g.TW);
@@ -402,7 +413,11 @@ struct BatchLayout {
   std::vector<size_t> scratch_off;
 };
 
-BatchLayout batch_layout(const geo_item *items, int n) {
+// The layout holds the geometry of the policy `sync`; its offsets and queue
+// capacity are the same for every candidate policy (the capacity covers the
+// most tiles any of them plans), so that a workspace sized once serves every
+// policy and geo_batch_launch need not know which one prepared it.
+BatchLayout batch_layout(const geo_item *items, int n, double sync) {
   BatchLayout L;
   const size_t nn = (size_t)(n > 0 ? n : 1);
   size_t off = 0;
@@ -414,9 +429,14 @@ BatchLayout batch_layout(const geo_item *items, int n) {
   off += up256(sizeof(BQueue));
   unsigned long long tiles = 0;
   L.geom.resize(n);
-  for (int i = 0; i < n; ++i) {
-    L.geom[i] = item_geometry(items[i]);
-    tiles += (unsigned long long)L.geom[i].tiles_x * (unsigned long long)L.geom[i].tiles_y;
+  for (int i = 0; i < n; ++i) L.geom[i] = item_geometry(items[i], sync);
+  for (int c = 0; c < kNumBatchSyncs; ++c) {
+    unsigned long long t = 0;
+    for (int i = 0; i < n; ++i) {
+      const Geometry g = item_geometry(items[i], kBatchSyncs[c]);
+      t += (unsigned long long)g.tiles_x * (unsigned long long)g.tiles_y;
+    }
+    if (t > tiles) tiles = t;
   }
   L.cap = 2 * tiles + 64;
   L.off_seq = off;
@@ -465,17 +485,22 @@ int check_items(const geo_item *items, int n) {
 
 extern "C" {
 
-size_t geo_batch_workspace_size(const geo_item *items, int n) {
-  if (check_items(items, n) != GEO_OK) return 0;
-  return batch_layout(items, n).total;
-}
+}  // extern "C"
 
-int geo_batch_prepare(const geo_item *items, int n, void *workspace, size_t ws_bytes, void *stream) {
+namespace {
+
+// geo_batch_prepare with the planner's per-pass charge `sync`
+int prepare_with(const geo_item *items, int n, void *workspace, size_t ws_bytes, void *stream, double sync) {
   int rc = check_items(items, n);
   if (rc != GEO_OK) return rc;
   if (!workspace) return GEO_ERR_ARG;
-  const BatchLayout L = batch_layout(items, n);
+  const BatchLayout L = batch_layout(items, n, sync);
   if (ws_bytes < L.total) return GEO_ERR_WORKSPACE;
+  // set up the device's library state here (its first use allocates), so
+  // that geo_batch_launch allocates nothing and can be captured in a graph
+  int *dev_status = nullptr;
+  rc = device_status_word(&dev_status);
+  if (rc != GEO_OK) return rc;
   std::vector<BItem> table(n);
   std::vector<double> cost(n);
   for (int i = 0; i < n; ++i) {
@@ -543,21 +568,33 @@ int geo_batch_prepare(const geo_item *items, int n, void *workspace, size_t ws_b
   return GEO_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+size_t geo_batch_workspace_size(const geo_item *items, int n) {
+  if (check_items(items, n) != GEO_OK) return 0;
+  return batch_layout(items, n, kBatchSyncs[0]).total;  // the same for every policy
+}
+
+int geo_batch_prepare(const geo_item *items, int n, void *workspace, size_t ws_bytes, void *stream) {
+  return prepare_with(items, n, workspace, ws_bytes, stream, tuned_batch_sync());
+}
+
 int geo_batch_launch(const geo_item *items, int n, void *workspace, int *status_out, void *stream) {
   int rc = check_items(items, n);
   if (rc != GEO_OK) return rc;
   if (!workspace) return GEO_ERR_ARG;
   if (n == 0) return GEO_OK;
-  const BatchLayout L = batch_layout(items, n);
+  // offsets and queue capacity only (the same for every policy)
+  const BatchLayout L = batch_layout(items, n, kBatchSyncs[0]);
   int *dev_status = nullptr;
   rc = device_status_word(&dev_status);
   if (rc != GEO_OK) return rc;
   BatchArgs A = batch_args(L, n, workspace, status_out, dev_status);
   cudaStream_t s = (cudaStream_t)stream;
   const int *order = (const int *)((char *)workspace + L.off_order);
-  unsigned long long ntasks0 = 0;
-  for (const Geometry &g : L.geom) ntasks0 += (unsigned long long)g.tiles_x * (unsigned long long)g.tiles_y;
-  batch_init<<<64, 256, 0, s>>>(A, order, ntasks0);
+  batch_init<<<64, 256, 0, s>>>(A, order);
   if (cudaGetLastError() != cudaSuccess) return GEO_ERR_CUDA;
   int dev = 0, nsm = 0, bps = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return GEO_ERR_CUDA;
@@ -573,6 +610,56 @@ int geo_batch_launch(const geo_item *items, int n, void *workspace, int *status_
   if (cudaLaunchCooperativeKernel((void *)batch_kernel, dim3(grid), dim3(kBatchNW * 32), args, 0, s) != cudaSuccess)
     return GEO_ERR_CUDA;
   return GEO_OK;
+}
+
+int geo_batch_autotune(const geo_item *items, int n, void *workspace, size_t ws_bytes, int *status_out,
+                       void *stream, const char *cache_path) {
+  int rc = check_items(items, n);
+  if (rc != GEO_OK) return rc;
+  if (!workspace || n == 0) return n == 0 ? GEO_OK : GEO_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return GEO_ERR_CUDA;
+  std::vector<int> st(status_out ? n : 0);
+  double best_sync = 0;
+  float best_ms = 1e30f;
+  for (int c = 0; c < kNumBatchSyncs && rc == GEO_OK; ++c) {
+    rc = prepare_with(items, n, workspace, ws_bytes, stream, kBatchSyncs[c]);
+    if (rc == GEO_OK) rc = geo_batch_launch(items, n, workspace, status_out, stream);  // warm-up
+    if (rc != GEO_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 2 && rc == GEO_OK; ++r) rc = geo_batch_launch(items, n, workspace, status_out, stream);
+    cudaEventRecord(e1, s);
+    if (rc != GEO_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = rc != GEO_OK ? rc : GEO_ERR_CUDA;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= 2;
+    // a policy under which an item did not complete is not a candidate
+    bool ok = true;
+    if (status_out) {
+      if (cudaMemcpy(st.data(), status_out, sizeof(int) * n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        rc = GEO_ERR_CUDA;
+        break;
+      }
+      for (int v : st) ok &= (v == GEO_OK || v == GEO_ERR_NOT_CONVERGED);
+    }
+    if (ok && ms < best_ms) {
+      best_ms = ms;
+      best_sync = kBatchSyncs[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != GEO_OK) return rc;
+  if (best_sync <= 0) return GEO_ERR_CUDA;
+  set_tuned_batch_sync(best_sync, best_ms);
+  // leave the workspace prepared with the chosen policy
+  rc = prepare_with(items, n, workspace, ws_bytes, stream, best_sync);
+  if (rc == GEO_OK && cache_path && cache_path[0]) rc = geo_tune_save(cache_path);
+  return rc;
 }
 
 int geo_batch(const geo_item *items, int n, void *workspace, size_t ws_bytes, int *status_out, void *stream) {

@@ -140,6 +140,10 @@ inline bool single_tile(const Plan &P, int batch) { return batch <= 1 && P.tiles
 int tuned_k(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps);
 // Tuned (K, variant) over every kernel shape; false when there is no entry.
 bool tuned_plan(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps, int *K, int *variant);
+// The batch planner's per-pass charge chosen by geo_batch_autotune (10 when
+// untuned), and its setter (geo_tune.cu).
+double tuned_batch_sync();
+void set_tuned_batch_sync(double sync, float ms);
 
 // Stream-ordered scratch from the library's per-device pool (geo_api.cu).
 int pool_alloc(void **p, size_t n, cudaStream_t s);

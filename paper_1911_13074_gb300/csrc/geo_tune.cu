@@ -19,6 +19,7 @@
 // File (version 2): a header "geomorph-tune 2 <device name>", then lines
 //   E dtype op conn height width steps_class K variant ms K0 ms0
 //   C dtype op conn hclass wclass steps_class K variant ms K0 ms0 work
+//   B sync ms            (the batch planner's per-pass charge, geo_batch.cu)
 // Version-1 files ("dtype op conn height width steps_class K ms") load as
 // exact entries of the default shape. Entries written on a different device
 // name are ignored when GEOMORPH_TUNE_CACHE is loaded.
@@ -48,6 +49,9 @@ struct TuneVal {
 
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_exact, g_class;
+// the batch planner's per-pass charge (geo_batch_autotune); 0: untuned
+double g_batch_sync = 0;
+float g_batch_ms = 0;
 
 int64_t steps_class(int op, int64_t steps) {
   if (op == 2 || op == 3) return -1;
@@ -104,6 +108,14 @@ int load_file(const char *path, bool check_device) {
         g_exact[TuneKey{dt, op, conn, a, b, sc}] = TuneVal{K, 0, ms, K, ms, 0};
       continue;
     }
+    double bs = 0;
+    if (sscanf(line, " B %lf %f", &bs, &ms) >= 1) {
+      if (bs > 0) {
+        g_batch_sync = bs;
+        g_batch_ms = ms;
+      }
+      continue;
+    }
     const int n = sscanf(line, " %c %d %d %d %lld %lld %lld %d %d %f %d %f %lf", &kind, &dt, &op, &conn, &a, &b, &sc,
                          &K, &v, &ms, &K0, &ms0, &work);
     if (n < 12 || K <= 0 || v < 0 || v >= kRRVariants) continue;
@@ -139,6 +151,7 @@ int write_file(const char *path) {
               (long long)std::get<5>(k), v.K, v.variant, v.ms, v.K0, v.ms0, v.work);
     }
   }
+  if (g_batch_sync > 0) fprintf(f, "B %.4f %.4f\n", g_batch_sync, g_batch_ms);
   fclose(f);
   return GEO_OK;
 }
@@ -169,6 +182,18 @@ bool tuned_plan(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps, i
   *K = v->K;
   *variant = v->variant;
   return true;
+}
+
+double tuned_batch_sync() {
+  load_env_once();
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_batch_sync > 0 ? g_batch_sync : 10.0;
+}
+
+void set_tuned_batch_sync(double sync, float ms) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_batch_sync = sync;
+  g_batch_ms = ms;
 }
 
 }  // namespace geo
@@ -276,7 +301,14 @@ int geo_tune_reset(void) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_exact.clear();
   g_class.clear();
+  g_batch_sync = 0;
+  g_batch_ms = 0;
   return GEO_OK;
+}
+
+int geo_tune_save(const char *cache_path) {
+  if (!cache_path) return GEO_ERR_ARG;
+  return write_file(cache_path);
 }
 
 int geo_tune_lookup(int dtype, int op, int conn, int64_t height, int64_t width, int64_t steps) {

@@ -27,3 +27,25 @@ def test_probe_takes_the_faster_form():
     rate, mhz, form = bench.probe_alu(FakeLib())
     assert (rate, mhz, form) == (64.1, 2069.0, "f16x2")
 
+
+def test_traffic_record_from_an_ncu_csv(tmp_path):
+    """The record is parsed from the capture's CSV (base units), the traffic
+    is read + write, and the stamp is the hash of the current sources, which
+    is what makes bench.py report the record's traffic."""
+    csv = tmp_path / "traffic.csv"
+    csv.write_text(
+        '==PROF== Connected to process 1\n'
+        '"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size",'
+        '"Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"\n'
+        '"0","1","python","h","void geo::rr_kernel<A, 8, true>(geo::TileLaunch)","1","7","(512, 1, 1)",'
+        '"(144, 1, 1)","0","10.3","Command line profiler metrics","dram__bytes_read.sum","byte","2,212,352"\n'
+        '"0","1","python","h","void geo::rr_kernel<A, 8, true>(geo::TileLaunch)","1","7","(512, 1, 1)",'
+        '"(144, 1, 1)","0","10.3","Command line profiler metrics","dram__bytes_write.sum","byte","370,432"\n'
+        '"0","1","python","h","void geo::rr_kernel<A, 8, true>(geo::TileLaunch)","1","7","(512, 1, 1)",'
+        '"(144, 1, 1)","0","10.3","Command line profiler metrics","gpu__time_duration.sum","nsecond","713,000"\n')
+    out = tmp_path / "rec.json"
+    rec = bench.write_traffic_record(str(csv), str(out))
+    assert rec["traffic_bytes_per_launch"] == 2212352 + 370432
+    assert rec["gpu_time_ms_under_ncu"] == pytest.approx(0.713)
+    assert rec["source_sha256"] == bench.kernel_source_sha256()
+    assert "rr_kernel" in rec["kernel"]

@@ -1,6 +1,8 @@
 """GPU parity of batched execution: every item of a batch equals its
 single-item result (bit-exact), across element types, operations,
 connectivities, lengths, reconstruction and windows, in one launch."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -149,3 +151,60 @@ def test_workload3_sample_matches_single_item_calls():
     b = gm().Batch(items)
     b.run()
     check(b, host)
+
+
+def test_launch_captured_as_a_fresh_process_first_library_work():
+    """In a process whose first library work is a batch, prepare() sets up
+    the device state, so that the launch captured right after it allocates
+    nothing inside the capture."""
+    import subprocess
+    import sys
+    code = """
+import numpy as np, torch, sys
+sys.path.insert(0, %r)
+import paper_1911_13074_gb300 as m, oracle, synth
+w = synth.workload0(150, 170)
+f, g = torch.from_numpy(w['marker']).cuda(), torch.from_numpy(w['mask']).cuda()
+b = m.Batch([{'op': 'dilate_chain', 'marker': f, 'mask': g, 'steps': 40, 'conn': 8}]).prepare()
+s = torch.cuda.Stream(); s.wait_stream(torch.cuda.current_stream())
+gr = torch.cuda.CUDAGraph()
+with torch.cuda.graph(gr, stream=s):
+    b.launch()
+torch.cuda.current_stream().wait_stream(s)
+gr.replay(); b.check()
+assert np.array_equal(b.outs[0].cpu().numpy(), oracle.chain(w['marker'], w['mask'], 40))
+print('fresh-capture-ok')
+""" % (os.path.dirname(os.path.dirname(os.path.abspath(__file__))),)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    assert "fresh-capture-ok" in r.stdout, r.stdout + r.stderr
+
+
+def test_batch_autotune_persists_a_policy_and_stays_exact(tmp_path):
+    """geo_batch_autotune times the batch under each candidate pass-length
+    policy, keeps the fastest (written to the tune file as a B line), leaves
+    the workspace prepared with it, and a new batch prepared afterwards uses
+    it; every item still equals the oracle."""
+    m = gm()
+    m.tune_reset()
+    try:
+        rng = np.random.default_rng(31)
+        items, host = random_items(rng, 24, 400, 300)
+        b = m.Batch(items)
+        path = tmp_path / "tune.txt"
+        b.autotune(path)
+        lines = path.read_text().splitlines()
+        blines = [ln for ln in lines if ln.startswith("B ")]
+        assert len(blines) == 1
+        assert float(blines[0].split()[1]) in (2.5, 5.0, 10.0, 20.0, 40.0, 80.0)
+        b.launch()
+        check(b, host)
+        b2 = m.Batch(items)
+        b2.run()
+        check(b2, host)
+        m.tune_reset()
+        m.tune_load(path)  # the policy comes back from the file
+        b3 = m.Batch(items)
+        b3.run()
+        check(b3, host)
+    finally:
+        m.tune_reset()

@@ -114,8 +114,9 @@ def test_workload2_full_size_reconstruction(kind):
 def test_workload3_every_item_against_oracle_digests():
     """The 512 items batched (the prepared launch captured in a CUDA graph and
     replayed, as the benchmark times it), as 512 single-item calls, and
-    batched again after autotuning the items (shape variant and K per item
-    and size class): every output against its oracle digest."""
+    batched again after autotuning (the items' single-image plans, then the
+    batch planner's policy on the batch itself): every output against its
+    oracle digest."""
     m = gm()
     digests = json.load(open(GOLDEN3))["cases"]
     items = []
@@ -155,6 +156,7 @@ def test_workload3_every_item_against_oracle_digests():
     compare(singles, "single-item calls")
     try:
         m.autotune(items)
+        m.Batch(items).autotune()
         compare(batched_graph(), "batched (autotuned plans)")
     finally:
         m.tune_reset()
