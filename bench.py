@@ -232,6 +232,67 @@ def alu_peak_top_s(nsm, lanes_per_clk, mhz):
     return nsm * lanes_per_clk * 2 * mhz * 1e6 / 1e12
 
 
+# Fewest instructions per pixel-step of the fastest exact min/max form of
+# each element path: uint8, two pixels per packed instruction, 5 operations
+# a masked step (2 row + 2 column extremes + the clamp) and 4 unmasked; float32
+# (and float64 through its ranks), one pixel per instruction, a 3-extreme in
+# one three-input max.f32: 3 instructions a masked step, 2 unmasked.
+INSTR_PER_PX_STEP = {("u8", True): 2.5, ("u8", False): 2.0, ("f32", True): 3.0, ("f32", False): 2.0}
+
+
+def peak_px_steps(nsm, rate, mhz, kind, masked):
+    """Peak pixel-steps per second of an element path: SMs x measured
+    min/max rate (lanes per SM clock) x clock / instructions per pixel-step."""
+    return nsm * rate * mhz * 1e6 / INSTR_PER_PX_STEP[(kind, masked)]
+
+
+def dtype_fractions(sec, nsm, u8_rate, f32_rate, mhz):
+    """Roofline fractions of the secondary measurements, each against its
+    element path's peak (peak_px_steps)."""
+    out = {}
+    w1 = sec.get("workload1_1024", {})
+    for name, v in w1.items():
+        if not isinstance(v, dict):
+            continue
+        parts = name.split("_")
+        kind, masked = parts[1], parts[0] == "chain"
+        if kind == "f64":
+            steps = int(parts[-1][5:]) if masked else int(parts[-1][1:])
+            if not masked or steps < 256:
+                continue  # int64-key path (no probed rate); the rank path runs the float32 kernel
+            kind = "f32"
+        peak = peak_px_steps(nsm, u8_rate if kind == "u8" else f32_rate, mhz, kind, masked)
+        out[name] = {"gpixel_steps_per_s": v["gpixel_steps_per_s"], "peak_gpixel_steps_per_s": peak / 1e9,
+                     "frac": v["gpixel_steps_per_s"] * 1e9 / peak,
+                     "path": "float32 kernel on ranks (rank transform included in the time)"
+                     if parts[1] == "f64" else kind}
+    rec = sec.get("reconstruct_4096", {})
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "workload2_sha256.json")) as fh:
+            golden = json.load(fh)["cases"]
+    except (OSError, ValueError):
+        golden = {}
+    for kind in ("u8", "f32"):
+        for name, gname in (("opening_31x31", "open15"), ("hdome_minus20", "hdome20")):
+            v, g = rec.get(f"{kind}_{name}"), golden.get(f"rec_{kind}_{gname}_conn8")
+            if not v or not g:
+                continue
+            # the plain method's work: every pixel for every changing step plus the step that changes nothing
+            px = 4096 * 4096 * (g["oracle_changing_steps"] + 1)
+            achieved = px / (v["ms"] / 1e3)
+            peak = peak_px_steps(nsm, u8_rate if kind == "u8" else f32_rate, mhz, kind, True)
+            out[f"reconstruct_4096_{kind}_{name}"] = {
+                "algorithmic_steps": g["oracle_changing_steps"] + 1, "gpixel_steps_per_s": achieved / 1e9,
+                "peak_gpixel_steps_per_s": peak / 1e9, "frac": achieved / peak}
+    fb = sec.get("fwd_bwd")
+    if fb:
+        peak = peak_px_steps(nsm, f32_rate, mhz, "f32", True)
+        out["workload4_plain_forward_f32"] = {"gpixel_steps_per_s": fb["plain_forward_gpixel_steps_per_s"],
+                                              "peak_gpixel_steps_per_s": peak / 1e9,
+                                              "frac": fb["plain_forward_gpixel_steps_per_s"] * 1e9 / peak}
+    return out
+
+
 def probe_alu(gm):
     """Lane-ops per SM clock of the faster packed min/max form, and the clock
     the probe ran at."""
@@ -664,6 +725,8 @@ def main():
         torch.cuda.synchronize(dev)
 
     alu_rate, alu_mhz, alu_form = probe_alu(gm)  # roofline denominator, before the warm-up
+    mix_rate, _ = gm.probe_minmax_rate("mix")  # the best two-pipe mix, the second denominator
+    f32_rate, _ = gm.probe_minmax_rate("f32x3")  # the float32 paths' denominators
     for _ in range(args.warmup):
         gm.dilate_chain(marker, mask, args.chain_steps, conn=CONN, out=out, check=False)
     torch.cuda.synchronize(dev)
@@ -745,10 +808,20 @@ def main():
                      "peak_basis": f"{nsm} SMs x {alu_rate:.1f} lane-ops/clk (max.{alu_form}, measured by "
                                    f"geo_probe_minmax_rate at {alu_mhz:.0f} MHz) x 2 px x {sm_max:.0f} MHz",
                      "ops_per_pixel_step": OPS_PER_PX_STEP,
+                     "mix_peak": alu_peak_top_s(nsm, mix_rate, sm_max),
+                     "frac_of_mix_peak": achieved / alu_peak_top_s(nsm, mix_rate, sm_max),
+                     "mix_basis": f"{mix_rate:.1f} maxima per SM clock for max.u16x2 mixed 2:1 with an exact "
+                                  f"FMA-pipe max (geo_probe_minmax_rate form 3)",
                      "issue_rate_peak": issue_peak, "frac_of_issue_rate_peak": achieved / issue_peak},
     }
     if not args.no_secondary and world == 1:
-        line.update(secondary(dev))
+        sec = secondary(dev)
+        line.update(sec)
+        line["fractions"] = {
+            "basis": f"per element path: {nsm} SMs x measured rate (u8 packed {alu_rate:.1f}, f32 three-input "
+                     f"{f32_rate:.1f} lane-ops per SM clock) x {sm_max:.0f} MHz / instructions per pixel-step "
+                     f"(u8 2.5 masked, 2 unmasked; f32 3 masked, 2 unmasked)",
+            **dtype_fractions(sec, nsm, alu_rate, f32_rate, sm_max)}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

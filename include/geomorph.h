@@ -393,9 +393,12 @@ GEO_API int geo_dilate_chain_noalloc(geo_dtype dtype, const void *marker, const 
                              int64_t steps, void *stream);
 
 /*
- * Measurement helper (not part of the method): the rate of the packed
- * min/max the uint8 step is built from (form 0: max.u16x2, form 1:
- * max.f16x2), for the ALU roofline of the benchmark. One block of 1024
+ * Measurement helper (not part of the method): the rate of the min/max the
+ * steps are built from, for the ALU rooflines of the benchmark. form 0:
+ * max.u16x2 and form 1: max.f16x2 (the uint8 step, two pixels a lane);
+ * form 2: three-input max.f32 (the float32 step's 3-extremes); form 3: a 2:1
+ * mix of max.u16x2 with an exact max of u16 lanes computed by two f16
+ * instructions on the FMA pipe (each maximum counted once). One block of 1024
  * threads per SM runs 16 independent chains of the instruction per thread;
  * lane_ops_per_clock receives the lane operations retired per SM clock
  * (averaged over the SMs, each SM timed by its own clock counter) and

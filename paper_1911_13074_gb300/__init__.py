@@ -309,10 +309,12 @@ def device_status(device=None) -> int:
 
 
 def probe_minmax_rate(form: str = "f16x2", device=None):
-    """Measured rate of the packed min/max of the uint8 step (form "u16x2" or
-    "f16x2") on this GPU: (lane-ops per SM clock, SM clock in MHz)."""
+    """Measured rate of a min/max form on this GPU: "u16x2" / "f16x2" (the
+    packed uint8 step), "f32x3" (three-input max.f32, the float32 step) or
+    "mix" (max.u16x2 with an FMA-pipe exact max, 2:1): (maxima per SM clock
+    per lane, SM clock in MHz)."""
     lib = load()
-    code = {"u16x2": 0, "f16x2": 1}[form]
+    code = {"u16x2": 0, "f16x2": 1, "f32x3": 2, "mix": 3}[form]
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
     rate, mhz = ctypes.c_double(0.0), ctypes.c_double(0.0)
     with torch.cuda.device(dev):

@@ -1,6 +1,7 @@
-// Throughput probe of the packed min/max the u8 chain is built from, for the
-// roofline of bench.py (a path bound by plain ALU arithmetic reports against
-// a peak derived from the unit rate and the clock).
+// Throughput probe of the min/max forms the chains are built from, for the
+// rooflines of bench.py (a path bound by plain ALU arithmetic reports against
+// a peak derived from the unit rate and the clock). A mixed form counts each
+// maximum once, whether it took one instruction or two.
 //
 // One 1024-thread block per SM (the dynamic shared memory request keeps a
 // second block off), each thread running NACC independent chains of the
@@ -20,12 +21,28 @@ constexpr int kProbeIters = 2048;
 constexpr int kProbeThreads = 1024;
 constexpr int kProbeSmem = 150 * 1024;
 
+// Form 0: max.u16x2; 1: max.f16x2; 2: three-input max.f32 (the float32
+// step's row and column 3-extremes); 3: a 2:1 mix of max.u16x2 and an exact
+// max of u16 lanes done by f16 arithmetic on the FMA pipe (fma.relu then
+// fma, two instructions), the fastest mix of two pipes measured. Chain i of
+// a thread uses the second form of the mix when i % 3 == 2.
 template <int FORM>
-__device__ __forceinline__ void probe_op(uint32_t &a, uint32_t b) {
-  if constexpr (FORM == 0)
+__device__ __forceinline__ void probe_op(uint32_t &a, uint32_t b, int i) {
+  if constexpr (FORM == 0) {
     asm volatile("max.u16x2 %0, %0, %1;" : "+r"(a) : "r"(b));
-  else
+  } else if constexpr (FORM == 1) {
     asm volatile("max.f16x2 %0, %0, %1;" : "+r"(a) : "r"(b));
+  } else if constexpr (FORM == 2) {
+    asm volatile("max.f32 %0, %0, %1, %0;" : "+r"(a) : "r"(b));
+  } else {
+    if (i % 3 != 2) {
+      asm volatile("max.u16x2 %0, %0, %1;" : "+r"(a) : "r"(b));
+    } else {
+      uint32_t r;
+      asm volatile("fma.rn.relu.f16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(b), "r"(0xBC00BC00u), "r"(a));
+      asm volatile("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(a) : "r"(r), "r"(0x3C003C00u), "r"(b));
+    }
+  }
 }
 
 template <int FORM>
@@ -39,7 +56,7 @@ __global__ void __launch_bounds__(kProbeThreads, 1) probe_kernel(unsigned long l
 #pragma unroll 1
   for (int it = 0; it < kProbeIters; ++it) {
 #pragma unroll
-    for (int i = 0; i < kProbeAcc; ++i) probe_op<FORM>(a[i], b);
+    for (int i = 0; i < kProbeAcc; ++i) probe_op<FORM>(a[i], b, i);
   }
   __syncthreads();
   const unsigned long long c1 = clock64(), g1 = globaltimer_ns();
@@ -101,12 +118,16 @@ int run_probe(int nsm, cudaStream_t st, double *rate, double *mhz) {
 extern "C" GEO_API int geo_probe_minmax_rate(int form, double *lane_ops_per_clock, double *clock_mhz,
                                              void *stream) {
   using namespace geo;
-  if ((form != 0 && form != 1) || !lane_ops_per_clock || !clock_mhz) return GEO_ERR_ARG;
+  if (form < 0 || form > 3 || !lane_ops_per_clock || !clock_mhz) return GEO_ERR_ARG;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
     return GEO_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  return form == 0 ? run_probe<0>(nsm, st, lane_ops_per_clock, clock_mhz)
-                   : run_probe<1>(nsm, st, lane_ops_per_clock, clock_mhz);
+  switch (form) {
+    case 0: return run_probe<0>(nsm, st, lane_ops_per_clock, clock_mhz);
+    case 1: return run_probe<1>(nsm, st, lane_ops_per_clock, clock_mhz);
+    case 2: return run_probe<2>(nsm, st, lane_ops_per_clock, clock_mhz);
+    default: return run_probe<3>(nsm, st, lane_ops_per_clock, clock_mhz);
+  }
 }

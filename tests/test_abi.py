@@ -66,7 +66,8 @@ def test_probe_rejects_bad_arguments_on_the_host():
     import paper_1911_13074_gb300 as gm
     lib = gm.load()
     r, c = ctypes.c_double(), ctypes.c_double()
-    assert lib.geo_probe_minmax_rate(2, ctypes.byref(r), ctypes.byref(c), None) == -1
+    assert lib.geo_probe_minmax_rate(4, ctypes.byref(r), ctypes.byref(c), None) == -1
+    assert lib.geo_probe_minmax_rate(-1, ctypes.byref(r), ctypes.byref(c), None) == -1
     assert lib.geo_probe_minmax_rate(0, None, ctypes.byref(c), None) == -1
 
 
@@ -88,6 +89,40 @@ def test_tune_cache_file_round_trip(tmp_path):
     import pytest as _pt
     with _pt.raises(gm.GeoError):
         gm.tune_load(bad)
+
+
+def test_tune_cache_version_2_round_trip(tmp_path):
+    """Version 2: exact entries (E) with a shape variant and the default
+    shape's K, size-class entries (C, half-octave classes floor(2 log2 n))
+    that other sizes of the class take, and the batch policy (B); a save
+    writes the same table back; reset empties it (no device needed)."""
+    import paper_1911_13074_gb300 as gm
+    gm.tune_reset()
+    try:
+        path = tmp_path / "tune.txt"
+        path.write_text("geomorph-tune 2 Some_GPU\n"
+                        "E 0 0 8 300 260 64 12 1 0.40 16 0.45\n"
+                        "C 0 0 8 16 16 64 12 1 0.40 16 0.45 1000\n"
+                        "C 1 3 4 20 21 -1 8 2 1.00 20 1.20 5000\n"
+                        "B 20.0 110.5\n")
+        gm.tune_load(path)
+        assert gm.tune_lookup(0, 0, 8, 300, 260, 1500) == 16      # the default shape's K
+        assert gm.tune_lookup(0, 0, 8, 330, 300, 700) == 16       # same classes: 2 log2 330 = 16.7
+        assert gm.tune_lookup(0, 0, 8, 400, 260, 700) == 0        # 2 log2 400 = 17.3: another class
+        assert gm.tune_lookup(1, "erode_rec", 4, 1024, 1500, 0) == 20  # classes 20 and 21
+        out = tmp_path / "saved.txt"
+        gm.tune_save(out)
+        lines = out.read_text().splitlines()
+        assert lines[0].startswith("geomorph-tune 2 ")
+        assert "E 0 0 8 300 260 64 12 1 0.4000 16 0.4500 0" in lines
+        assert any(ln.startswith("C 1 3 4 20 21 -1 8 2 ") for ln in lines)
+        assert any(ln.startswith("B 20.0000 ") for ln in lines)
+        gm.tune_reset()
+        assert gm.tune_lookup(0, 0, 8, 300, 260, 1500) == 0
+        gm.tune_load(out)
+        assert gm.tune_lookup(0, 0, 8, 330, 300, 700) == 16
+    finally:
+        gm.tune_reset()
 
 
 def test_missing_library_fails_loudly():

@@ -49,3 +49,27 @@ def test_traffic_record_from_an_ncu_csv(tmp_path):
     assert rec["gpu_time_ms_under_ncu"] == pytest.approx(0.713)
     assert rec["source_sha256"] == bench.kernel_source_sha256()
     assert "rr_kernel" in rec["kernel"]
+
+
+def test_dtype_fractions_of_the_secondary_measurements():
+    """Each case against its element path's peak: uint8 at 2.5 instructions
+    per masked pixel-step (2 unmasked), float32 at 3 (2); float64 chains of
+    256 steps or more run the float32 kernel on ranks; reconstructions count
+    the plain method's work from the oracle's changing steps."""
+    sec = {"workload1_1024": {"workload": "x",
+                              "chain_u8_dilate_conn8_steps1500": {"ms": 0.72, "gpixel_steps_per_s": 2000.0},
+                              "window_u8_dilate_s13": {"ms": 0.02, "gpixel_steps_per_s": 600.0},
+                              "chain_f64_dilate_conn8_steps1500": {"ms": 1.6, "gpixel_steps_per_s": 950.0},
+                              "chain_f64_dilate_conn8_steps100": {"ms": 0.3, "gpixel_steps_per_s": 300.0}},
+           "reconstruct_4096": {"u8_opening_31x31": {"ms": 3.0, "steps_applied": 600}},
+           "fwd_bwd": {"plain_forward_gpixel_steps_per_s": 430.0}}
+    fr = bench.dtype_fractions(sec, 152, 64.0, 64.0, 2070.0)
+    u8_peak = 152 * 64 * 2070e6 / 2.5
+    assert fr["chain_u8_dilate_conn8_steps1500"]["frac"] == pytest.approx(2000e9 / u8_peak)
+    assert fr["window_u8_dilate_s13"]["frac"] == pytest.approx(600e9 / (152 * 64 * 2070e6 / 2.0))
+    assert fr["chain_f64_dilate_conn8_steps1500"]["frac"] == pytest.approx(950e9 / (152 * 64 * 2070e6 / 3.0))
+    assert "chain_f64_dilate_conn8_steps100" not in fr
+    rec = fr["reconstruct_4096_u8_opening_31x31"]
+    assert rec["algorithmic_steps"] == 573  # 572 changing steps in the oracle, plus the step that changes nothing
+    assert rec["frac"] == pytest.approx(4096 * 4096 * 573 / 3e-3 / u8_peak)
+    assert fr["workload4_plain_forward_f32"]["frac"] == pytest.approx(430e9 / (152 * 64 * 2070e6 / 3.0))

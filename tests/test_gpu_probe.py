@@ -1,9 +1,9 @@
-"""The min/max rate probe behind the benchmark's ALU roofline."""
+"""The min/max rate probe behind the benchmark's ALU rooflines."""
 import pytest
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("form", ["u16x2", "f16x2"])
+@pytest.mark.parametrize("form", ["u16x2", "f16x2", "f32x3", "mix"])
 def test_probe_reports_a_rate_within_the_issue_limit(form):
     import paper_1911_13074_gb300 as gm
     rate, mhz = gm.probe_minmax_rate(form)
