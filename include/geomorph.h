@@ -343,7 +343,8 @@ GEO_API int geo_plan_shape(geo_dtype dtype, int op, int conn, int64_t height, in
  *
  * geo_chain_backward_workspace_size: bytes of device workspace the pair
  *   below needs (checkpoints every ckpt_interval steps, 1 <= ckpt_interval
- *   <= 512, the recomputed states of one segment at every 8th step, two
+ *   <= 512; the recomputed states of one segment at every 8th step; the
+ *   routing codes of one segment, a 32-bit word per pixel and 8 steps; two
  *   gradient buffers); 0 for invalid arguments.
  * geo_chain_fwd_ckpt: out = the chain of `steps` steps (as geo_dilate_chain /
  *   geo_erode_chain), also storing the checkpoints in `workspace` (caller

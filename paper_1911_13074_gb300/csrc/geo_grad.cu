@@ -18,13 +18,19 @@
 //
 // Memory: the forward pass stores checkpoints f_{sC} every C steps
 // (geo_chain_fwd_ckpt). The backward pass walks the segments from last to
-// first. Per segment, the chain kernel recomputes the states at every 8th
-// step from the checkpoint; then, per sub-segment of up to 8 steps (last
-// first), one fused kernel per 64x64 tile (32x32 for float64) recomputes the
-// forward in shared memory from the sub-segment start, keeping one routing
-// byte per pixel and step (0..8 = neighbour, 9 = mask), and replays the
-// steps in reverse there: the gradient and grad_mask touch global memory
-// once per sub-segment instead of once per step.
+// first. Per segment, in sub-segments of up to 8 steps:
+//   * forward, first to last: a code kernel per 64x64 tile (32x32 for
+//     float64) recomputes the sub-segment in shared memory from its start
+//     state, on the tile plus an 8-pixel halo, and writes for each of the
+//     tile's pixels one 32-bit word holding its routing code at every step
+//     (4 bits a step: 0..8 = neighbour, 9 = mask) and its state at the end,
+//     the start of the next sub-segment;
+//   * reverse, last to first: a gather kernel per tile stages the gradient
+//     and the code words on the tile plus the 8-pixel halo and replays the
+//     steps in reverse there.
+// The gradient and grad_mask touch global memory once per sub-segment
+// instead of once per step, and no state is recomputed twice.
+#include <cstdlib>
 #include <cstring>
 
 #include "geo_common.cuh"
@@ -44,22 +50,8 @@ __device__ __forceinline__ bool in_shape(int k) {
 constexpr int kBX = 32, kBY = 8;
 
 // ---------------------------------------------------------------------------
-// fused segment kernel: forward recompute and reverse replay of up to SS
-// steps for one TT x TT tile, all in shared memory
+// helpers of the segment kernels
 // ---------------------------------------------------------------------------
-
-constexpr int kSegT = 32;                  // the CTA is kSegT x kSegT threads
-constexpr int kSegThreads = kSegT * kSegT;
-
-template <typename T, int TT, int SS>
-struct SegGeom {
-  static constexpr int RF = TT + 4 * SS;  // forward region side: the tile plus 2 SS
-  static constexpr int RB = TT + 2 * SS;  // reverse region side: the tile plus SS
-  static constexpr size_t f_bytes = sizeof(T) * RF * RF;
-  static constexpr size_t code_bytes = ((size_t)SS * RB * RB + 15) / 16 * 16;
-  static constexpr size_t g_bytes = sizeof(T) * RB * RB;
-  static constexpr size_t smem = 3 * f_bytes + code_bytes + 2 * g_bytes;
-};
 
 // Identity of the neighbourhood extreme: what cells outside the image hold
 // (image and mask) in the shared-memory regions, so that they never win an
@@ -100,78 +92,99 @@ struct RowExt {
   }
 };
 
-// The threads of a CTA as (column, chunk of rows) of a region of side R:
-// thread t takes column t % R and rows [chunk * RP, chunk * RP + RP).
-template <int R>
-struct Strips {
-  static constexpr int NH = kSegThreads / R;        // chunks
-  static constexpr int RP = (R + NH - 1) / NH;      // rows per chunk
+// ---------------------------------------------------------------------------
+// split segment kernels: (A) the routing codes of each tile's own pixels for
+// up to SS = 8 steps, packed into one 32-bit word per pixel (4 bits a step,
+// step j in bits 4(j-1)..4j-1) in a global code plane; (B) the reverse
+// replay of those steps from the staged code words. A tile's codes need the
+// segment-start state only within SS of the tile (TT + 2 SS), against
+// TT + 4 SS when one kernel computes the codes of the whole reverse region
+// itself; the code plane (4 bytes a pixel) stays in L2 between the two.
+// ---------------------------------------------------------------------------
+
+constexpr int kSplitThreads = 512;          // two CTAs per SM
+constexpr uint32_t kCodesNone = 0xffffffffu;  // outside the image: code 15 (routes nowhere) at every step
+
+template <typename T, int TT, int SS>
+struct SplitGeom {
+  static_assert(SS <= 8, "8 steps of 4-bit codes in a 32-bit word");
+  static constexpr int R = TT + 2 * SS;  // region side of both kernels
+  static constexpr int NS = (R * R + kSplitThreads - 1) / kSplitThreads;  // staging rounds per thread
+  static constexpr size_t f_bytes = sizeof(T) * R * R;
+  static constexpr size_t c_bytes = sizeof(uint32_t) * R * R;
+  static constexpr size_t a_smem = 3 * f_bytes;            // two states and the mask
+  static constexpr size_t b_smem = 2 * f_bytes + c_bytes;  // two gradients and the code words
 };
 
-// f0: the state at the segment start, packed (row stride W). S <= SS steps
-// t0+1 .. t0+S are recomputed; then g at t0+S (g_in) is carried back to t0
-// (g_out) and grad_mask gathers the mask-routed gradients of those steps in
-// decreasing step order (written, not accumulated, when `first`).
-//
-// Forward: every thread walks one column over its chunk of rows with a
-// sliding window of three row extremes, so each row extreme (and its lowest
-// dx) is computed once and used by three cells; the cell's neighbourhood
-// extreme is the first of the rows above / at / below that attains the
-// largest row extreme, which is the lowest index k = (dy+1)*3 + (dx+1) in
-// row-major order. Reverse: the same walk with a window of three rows of
-// routing codes and gradients; each cell adds the gradients routed to it in
-// increasing k.
+// The threads of a CTA as (column, chunk of rows) of a region of side R.
+template <int R, int NT>
+struct StripsN {
+  static constexpr int NH = NT / R;
+  static constexpr int RP = (R + NH - 1) / NH;
+};
+
+// (A) f0: the state at the sub-segment start (row stride W). Steps 1..S are
+// recomputed on the cells within SS - j of the tile at step j. A thread owns
+// the same cells (a column of a chunk of rows) at every step, so it keeps the
+// codes of its tile cells in registers and writes each cell's code word once.
 template <typename T, int OP, int CONN, int TT, int SS>
-__global__ void __launch_bounds__(kSegThreads) seg_backward(const T *__restrict__ f0, const T *__restrict__ mask,
-                                                            int64_t mpitch, const T *__restrict__ g_in,
-                                                            int64_t gi_pitch, T *__restrict__ g_out, int64_t go_pitch,
-                                                            T *__restrict__ gmask, int64_t gm_pitch, int H, int W,
-                                                            int S, int first) {
-  using G = SegGeom<T, TT, SS>;
-  constexpr int RF = G::RF, RB = G::RB;
-  using SF = Strips<RF>;
-  using SB = Strips<RB>;
+__global__ void __launch_bounds__(kSplitThreads, 2) seg_codes(const T *__restrict__ f0, const T *__restrict__ mask,
+                                                              int64_t mpitch, uint32_t *__restrict__ codes,
+                                                              T *__restrict__ f_next, int H, int W, int S) {
+  using G = SplitGeom<T, TT, SS>;
+  constexpr int R = G::R;
+  using SP = StripsN<R, kSplitThreads>;
   extern __shared__ __align__(16) char smem[];
   T *fa = reinterpret_cast<T *>(smem);
   T *fb = reinterpret_cast<T *>(smem + G::f_bytes);
   T *ms = reinterpret_cast<T *>(smem + 2 * G::f_bytes);
-  uint8_t *codes = reinterpret_cast<uint8_t *>(smem + 3 * G::f_bytes);
-  T *ga = reinterpret_cast<T *>(smem + 3 * G::f_bytes + G::code_bytes);
-  T *gb = reinterpret_cast<T *>(smem + 3 * G::f_bytes + G::code_bytes + G::g_bytes);
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kSegT + tx;
+  const int tid = threadIdx.x;
   const int b = blockIdx.z;
   const int ty0 = blockIdx.y * TT, tx0 = blockIdx.x * TT;
-  const int fy0 = ty0 - 2 * SS, fx0 = tx0 - 2 * SS;  // forward region origin (global)
-  const int by0 = ty0 - SS, bx0 = tx0 - SS;          // reverse region origin (global)
+  const int oy = ty0 - SS, ox = tx0 - SS;  // region origin (global)
   const T ID = seg_ident<T, OP>();
   const T *fimg = f0 + (size_t)b * H * W;
   const T *mimg = mask + (size_t)b * H * mpitch;
-  // stage f0 and the mask on the forward region (the identity outside the image)
-  for (int r = ty; r < RF; r += kSegT) {
-    const int y = fy0 + r;
-    for (int c = tx; c < RF; c += kSegT) {
-      const int x = fx0 + c;
-      const bool in = y >= 0 && y < H && x >= 0 && x < W;
-      fa[r * RF + c] = in ? fimg[(size_t)y * W + x] : ID;
-      ms[r * RF + c] = in ? mimg[(size_t)y * mpitch + x] : ID;
+  {
+    // every load of the thread in flight before the first store
+    T fv[G::NS], mv[G::NS];
+#pragma unroll
+    for (int it = 0; it < G::NS; ++it) {
+      const int i = tid + it * kSplitThreads;
+      const int r = i / R, c = i - r * R;
+      const int y = oy + r, x = ox + c;
+      const bool in = i < R * R && y >= 0 && y < H && x >= 0 && x < W;
+      fv[it] = in ? fimg[(size_t)y * W + x] : ID;
+      mv[it] = in ? mimg[(size_t)y * mpitch + x] : ID;
+    }
+#pragma unroll
+    for (int it = 0; it < G::NS; ++it) {
+      const int i = tid + it * kSplitThreads;
+      if (i < R * R) {
+        fa[i] = fv[it];
+        ms[i] = mv[it];
+      }
     }
   }
   __syncthreads();
-  // forward: step j computes the cells within 2SS - j of the tile and keeps
-  // the routing codes of the cells within SS of it
-  const int fcol = tid % RF, fchunk = tid / RF;
+  const int col = tid % R, chunk = tid / R;
+  const int base = chunk * SP::RP;
+  uint32_t cw[SP::RP];
+#pragma unroll
+  for (int q = 0; q < SP::RP; ++q) cw[q] = kCodesNone;
   T *cur = fa, *nxt = fb;
   for (int j = 1; j <= S; ++j) {
-    const int lo = j, hi = RF - j;  // rows / cols [lo, hi) of the forward region
-    uint8_t *ct = codes + (size_t)(j - 1) * RB * RB;
-    const int c = fcol;
-    const int r0 = max(lo, fchunk * SF::RP), r1 = min(hi, fchunk * SF::RP + SF::RP);
-    if (fchunk < SF::NH && c >= lo && c < hi && r0 < r1) {
+    const int lo = j, hi = R - j;
+    const int c = col;
+    const int r0 = max(lo, base), r1 = min(hi, base + SP::RP);
+    const int sh = 4 * (j - 1);
+    if (chunk < SP::NH && c >= lo && c < hi && r0 < r1) {
       RowExt<T, OP> up, mid, dn;
-      up.load(cur + (r0 - 1) * RF, c);
-      mid.load(cur + r0 * RF, c);
-      for (int r = r0; r < r1; ++r) {
-        dn.load(cur + (r + 1) * RF, c);
+      up.load(cur + (r0 - 1) * R, c);
+      mid.load(cur + r0 * R, c);
+      auto cell = [&](int q) {
+        const int r = base + q;
+        dn.load(cur + (r + 1) * R, c);
         T best;
         int k;
         if (CONN == 8) {
@@ -185,7 +198,7 @@ __global__ void __launch_bounds__(kSegThreads) seg_backward(const T *__restrict_
             best = dn.m;
             k = 6 + dn.a;
           }
-        } else {  // the cross: k = 1, 3, 4, 5, 7
+        } else {
           best = up.ctr;
           k = 1;
           if (beats<T, OP>(mid.m, best)) {
@@ -197,13 +210,22 @@ __global__ void __launch_bounds__(kSegThreads) seg_backward(const T *__restrict_
             k = 7;
           }
         }
-        const T mv = ms[r * RF + c];
-        const bool to_mask = beats<T, OP>(best, mv);  // mask strictly beyond the extreme
-        nxt[r * RF + c] = to_mask ? mv : best;
-        const int rb = r - SS, cb = c - SS;
-        if (rb >= 0 && rb < RB && cb >= 0 && cb < RB) ct[rb * RB + cb] = to_mask ? kRouteMask : (uint8_t)k;
+        const T mv = ms[r * R + c];
+        const bool to_mask = beats<T, OP>(best, mv);
+        nxt[r * R + c] = to_mask ? mv : best;
+        const uint32_t code = to_mask ? kRouteMask : (uint32_t)k;
+        cw[q] = (cw[q] & ~(15u << sh)) | (code << sh);
         up = mid;
         mid = dn;
+      };
+      if (r0 == base && r1 == base + SP::RP) {
+        // a whole chunk: straight-line code, the window rotation is renaming
+#pragma unroll
+        for (int q = 0; q < SP::RP; ++q) cell(q);
+      } else {
+#pragma unroll
+        for (int q = 0; q < SP::RP; ++q)
+          if (base + q >= r0 && base + q < r1) cell(q);
       }
     }
     __syncthreads();
@@ -211,75 +233,127 @@ __global__ void __launch_bounds__(kSegThreads) seg_backward(const T *__restrict_
     cur = nxt;
     nxt = tmp;
   }
-  // reverse: stage g at t0+S on the reverse region
-  const T *gimg = g_in + (size_t)b * H * gi_pitch;
-  for (int r = ty; r < RB; r += kSegT) {
-    const int y = by0 + r;
-    for (int c = tx; c < RB; c += kSegT) {
-      const int x = bx0 + c;
-      ga[r * RB + c] = (y >= 0 && y < H && x >= 0 && x < W) ? gimg[(size_t)y * gi_pitch + x] : T(0);
+  // the code words of the thread's tile cells, and (f_next) their state
+  // after the S steps: the start of the next sub-segment
+  const int x = ox + col;
+  if (chunk < SP::NH && col >= SS && col < SS + TT && x < W) {
+    uint32_t *cimg = codes + (size_t)b * H * W;
+    T *nimg = f_next ? f_next + (size_t)b * H * W : nullptr;
+#pragma unroll
+    for (int q = 0; q < SP::RP; ++q) {
+      const int r = base + q, y = oy + r;
+      if (r >= SS && r < SS + TT && y < H) {
+        cimg[(size_t)y * W + x] = cw[q];
+        if (nimg) nimg[(size_t)y * W + x] = cur[r * R + col];
+      }
     }
   }
-  // per thread: its fixed tile pixels' mask gradient, (ty + e * kSegT, tx + f * kSegT)
-  constexpr int PT = (TT + kSegT - 1) / kSegT;
-  T gmacc[PT][PT];
+}
+
+// (B) g at t0 + S (g_in) carried back to t0 (g_out) with the code words of
+// steps t0 + 1 .. t0 + S from (A); grad_mask gathers the mask-routed
+// gradients in decreasing step order (written, not accumulated, when `first`).
+template <typename T, int CONN, int TT, int SS>
+__global__ void __launch_bounds__(kSplitThreads, 2) seg_gather(const uint32_t *__restrict__ codes,
+                                                               const T *__restrict__ g_in, int64_t gi_pitch,
+                                                               T *__restrict__ g_out, int64_t go_pitch,
+                                                               T *__restrict__ gmask, int64_t gm_pitch, int H, int W,
+                                                               int S, int first) {
+  using G = SplitGeom<T, TT, SS>;
+  constexpr int R = G::R;
+  using SP = StripsN<R, kSplitThreads>;
+  extern __shared__ __align__(16) char smem[];
+  T *ga = reinterpret_cast<T *>(smem);
+  T *gb = reinterpret_cast<T *>(smem + G::f_bytes);
+  uint32_t *cs = reinterpret_cast<uint32_t *>(smem + 2 * G::f_bytes);
+  const int tid = threadIdx.x;
+  const int b = blockIdx.z;
+  const int ty0 = blockIdx.y * TT, tx0 = blockIdx.x * TT;
+  const int oy = ty0 - SS, ox = tx0 - SS;
+  const T *gimg = g_in + (size_t)b * H * gi_pitch;
+  const uint32_t *cimg = codes + (size_t)b * H * W;
+  {
+    T gv[G::NS];
+    uint32_t cv[G::NS];
+#pragma unroll
+    for (int it = 0; it < G::NS; ++it) {
+      const int i = tid + it * kSplitThreads;
+      const int r = i / R, c = i - r * R;
+      const int y = oy + r, x = ox + c;
+      const bool in = i < R * R && y >= 0 && y < H && x >= 0 && x < W;
+      gv[it] = in ? gimg[(size_t)y * gi_pitch + x] : T(0);
+      cv[it] = in ? cimg[(size_t)y * W + x] : kCodesNone;
+    }
+#pragma unroll
+    for (int it = 0; it < G::NS; ++it) {
+      const int i = tid + it * kSplitThreads;
+      if (i < R * R) {
+        ga[i] = gv[it];
+        cs[i] = cv[it];
+      }
+    }
+  }
+  // per thread: its fixed tile pixels' mask gradient
+  constexpr int PT = (TT * TT + kSplitThreads - 1) / kSplitThreads;
+  T gmacc[PT];
   T *gmimg = gmask + (size_t)b * H * gm_pitch;
 #pragma unroll
-  for (int e = 0; e < PT; ++e)
-#pragma unroll
-    for (int f = 0; f < PT; ++f) {
-      const int r = ty + e * kSegT, c = tx + f * kSegT;
-      const int y = ty0 + r, x = tx0 + c;
-      gmacc[e][f] = (!first && r < TT && c < TT && y < H && x < W) ? gmimg[(size_t)y * gm_pitch + x] : T(0);
-    }
+  for (int e = 0; e < PT; ++e) {
+    const int i = tid + e * kSplitThreads;
+    const int r = i / TT, c = i - r * TT;
+    const int y = ty0 + r, x = tx0 + c;
+    gmacc[e] = (!first && i < TT * TT && y < H && x < W) ? gmimg[(size_t)y * gm_pitch + x] : T(0);
+  }
   __syncthreads();
-  const int bcol = tid % RB, bchunk = tid / RB;
+  const int col = tid % R, chunk = tid / R;
   T *gc = ga, *gn = gb;
   for (int j = S; j >= 1; --j) {
-    const uint8_t *ct = codes + (size_t)(j - 1) * RB * RB;
-    // grad_mask of the tile at step t0 + j, in decreasing step order
+    const int sh = 4 * (j - 1);
 #pragma unroll
-    for (int e = 0; e < PT; ++e)
-#pragma unroll
-      for (int f = 0; f < PT; ++f) {
-        const int r = SS + ty + e * kSegT, c = SS + tx + f * kSegT;
-        if (ty + e * kSegT < TT && tx + f * kSegT < TT && ct[r * RB + c] == kRouteMask) gmacc[e][f] += gc[r * RB + c];
-      }
-    // g at t0 + j - 1 on the cells within j - 1 of the tile: cell q gathers
-    // g(p) from p = q - d_k for k = 0..8 where p routed to k; in row terms
-    // k = 0..2 read the row below (columns c+1, c, c-1), k = 3..5 the own
-    // row, k = 6..8 the row above
-    const int lo = SS - (j - 1), hi = RB - lo;
-    const int c = bcol;
-    const int r0 = max(lo, bchunk * SB::RP), r1 = min(hi, bchunk * SB::RP + SB::RP);
-    if (bchunk < SB::NH && c >= lo && c < hi && r0 < r1) {
-      // window: codes and gradients of rows r-1 (A), r (B), r+1 (C) at columns c+1, c, c-1
-      uint8_t kA[3], kB[3], kC[3];
+    for (int e = 0; e < PT; ++e) {
+      const int i = tid + e * kSplitThreads;
+      const int r = SS + i / TT, c = SS + i % TT;
+      if (i < TT * TT && ((cs[r * R + c] >> sh) & 15u) == kRouteMask) gmacc[e] += gc[r * R + c];
+    }
+    const int lo = SS - (j - 1), hi = R - lo;
+    const int c = col;
+    const int base = chunk * SP::RP;
+    const int r0 = max(lo, base), r1 = min(hi, base + SP::RP);
+    if (chunk < SP::NH && c >= lo && c < hi && r0 < r1) {
+      // window of three rows (r - 1, r, r + 1) of codes and gradients at
+      // columns c + 1, c, c - 1; the cell gathers, in increasing k, the
+      // gradients of the neighbours routed to it: k = 0..2 from the row
+      // below, 3..5 from its own row, 6..8 from the row above
+      uint32_t kA[3], kB[3], kC[3];
       T gA[3], gB[3], gC[3];
+      const uint32_t *crow = cs + (r0 - 1) * R + c - 1;
+      const T *grow = gc + (r0 - 1) * R + c - 1;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        kA[i] = ct[(r0 - 1) * RB + c + 1 - i];
-        gA[i] = gc[(r0 - 1) * RB + c + 1 - i];
-        kB[i] = ct[r0 * RB + c + 1 - i];
-        gB[i] = gc[r0 * RB + c + 1 - i];
+        kA[i] = (crow[2 - i] >> sh) & 15u;
+        gA[i] = grow[2 - i];
+        kB[i] = (crow[R + 2 - i] >> sh) & 15u;
+        gB[i] = grow[R + 2 - i];
       }
-      for (int r = r0; r < r1; ++r) {
+      auto cell = [&](int r) {
+        const uint32_t *cn = cs + (r + 1) * R + c - 1;
+        const T *gnr = gc + (r + 1) * R + c - 1;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          kC[i] = ct[(r + 1) * RB + c + 1 - i];
-          gC[i] = gc[(r + 1) * RB + c + 1 - i];
+          kC[i] = (cn[2 - i] >> sh) & 15u;
+          gC[i] = gnr[2 - i];
         }
         T acc = T(0);
 #pragma unroll
-        for (int i = 0; i < 3; ++i)  // k = i: p in the row below
-          if (in_shape<CONN>(i)) acc = kC[i] == i ? acc + gC[i] : acc;
+        for (int i = 0; i < 3; ++i)
+          if (in_shape<CONN>(i) && kC[i] == (uint32_t)i) acc += gC[i];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)  // k = 3 + i: the own row
-          if (in_shape<CONN>(3 + i)) acc = kB[i] == 3 + i ? acc + gB[i] : acc;
+        for (int i = 0; i < 3; ++i)
+          if (in_shape<CONN>(3 + i) && kB[i] == (uint32_t)(3 + i)) acc += gB[i];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)  // k = 6 + i: the row above
-          if (in_shape<CONN>(6 + i)) acc = kA[i] == 6 + i ? acc + gA[i] : acc;
-        gn[r * RB + c] = acc;
+        for (int i = 0; i < 3; ++i)
+          if (in_shape<CONN>(6 + i) && kA[i] == (uint32_t)(6 + i)) acc += gA[i];
+        gn[r * R + c] = acc;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
           kA[i] = kB[i];
@@ -287,6 +361,13 @@ __global__ void __launch_bounds__(kSegThreads) seg_backward(const T *__restrict_
           kB[i] = kC[i];
           gB[i] = gC[i];
         }
+      };
+      if (r0 == base && r1 == base + SP::RP) {
+        // a whole chunk: straight-line code, the window rotation is renaming
+#pragma unroll
+        for (int q = 0; q < SP::RP; ++q) cell(base + q);
+      } else {
+        for (int r = r0; r < r1; ++r) cell(r);
       }
     }
     __syncthreads();
@@ -294,19 +375,17 @@ __global__ void __launch_bounds__(kSegThreads) seg_backward(const T *__restrict_
     gc = gn;
     gn = tmp;
   }
-  // write g at t0 and grad_mask for the tile
   T *goimg = g_out + (size_t)b * H * go_pitch;
 #pragma unroll
-  for (int e = 0; e < PT; ++e)
-#pragma unroll
-    for (int f = 0; f < PT; ++f) {
-      const int r = ty + e * kSegT, c = tx + f * kSegT;
-      const int y = ty0 + r, x = tx0 + c;
-      if (r < TT && c < TT && y < H && x < W) {
-        goimg[(size_t)y * go_pitch + x] = gc[(SS + r) * RB + SS + c];
-        gmimg[(size_t)y * gm_pitch + x] = gmacc[e][f];
-      }
+  for (int e = 0; e < PT; ++e) {
+    const int i = tid + e * kSplitThreads;
+    const int r = i / TT, c = i - r * TT;
+    const int y = ty0 + r, x = tx0 + c;
+    if (i < TT * TT && y < H && x < W) {
+      goimg[(size_t)y * go_pitch + x] = gc[(SS + r) * R + SS + c];
+      gmimg[(size_t)y * gm_pitch + x] = gmacc[e];
     }
+  }
 }
 
 template <typename T>
@@ -316,15 +395,10 @@ __global__ void __launch_bounds__(kBX * kBY) zero_plane(T *__restrict__ p, int64
   p[(size_t)blockIdx.z * H * pitch + (size_t)y * pitch + x] = T(0);
 }
 
-// Sub-segment length of the fused kernel and its tile side per element type.
-// 8 steps measured best on workload 4 (17.2 ms forward + backward; 6 steps
-// 19.3 ms, 4 steps 20.6 ms: the halos shrink but launches and staging
-// double); longer sub-segments do not fit 227 KB of shared memory at a
-// 64-pixel tile.
-#ifndef GEO_SEG_STEPS
-#define GEO_SEG_STEPS 8
-#endif
-constexpr int kSeg = GEO_SEG_STEPS;
+// Sub-segment length (8 codes of 4 bits fill a 32-bit word) and the tile
+// side per element type: both kernels then hold two CTAs per SM (77 KB of
+// shared memory each for float32).
+constexpr int kSeg = 8;
 constexpr int kTileF32 = 64, kTileF64 = 32;
 
 struct Layout {
@@ -332,7 +406,7 @@ struct Layout {
   int64_t nseg;   // checkpoints (segments of C steps)
   int64_t nsub;   // sub-segment starts kept per segment (C / kSeg, rounded up)
   size_t ckpt_b;  // bytes of one packed state (all images)
-  size_t off_ckpt, off_state0, off_state1, off_sub, off_g0, off_g1, total;
+  size_t off_ckpt, off_state0, off_state1, off_sub, off_g0, off_g1, off_codes, total;
 };
 
 Layout layout(int es, int64_t H, int64_t W, int64_t steps, int C, int batch) {
@@ -349,23 +423,39 @@ Layout layout(int es, int64_t H, int64_t W, int64_t steps, int C, int batch) {
   L.off_sub = L.off_state1 + st;
   L.off_g0 = L.off_sub + st * (size_t)L.nsub;
   L.off_g1 = L.off_g0 + st;
-  L.total = L.off_g1 + st;
+  // routing codes of every sub-segment of a segment, a 32-bit word per pixel
+  // each (split kernels)
+  L.off_codes = L.off_g1 + st;
+  L.total = L.off_codes + up((size_t)L.npx * sizeof(uint32_t)) * (size_t)L.nsub;
   return L;
 }
 
 template <typename T, int TT>
-int launch_seg(int op, int conn, const T *f0, const T *mask, int64_t mpitch, const T *gin, int64_t gi_pitch, T *gout,
-               int64_t go_pitch, T *gm, int64_t gm_pitch, int H, int W, int batch, int S, int first, cudaStream_t s) {
-  using Gm = SegGeom<T, TT, kSeg>;
+int launch_codes(int op, int conn, const T *f0, const T *mask, int64_t mpitch, uint32_t *codes, T *f_next, int H,
+                 int W, int batch, int S, cudaStream_t s) {
+  using Gm = SplitGeom<T, TT, kSeg>;
   const dim3 grid((unsigned)((W + TT - 1) / TT), (unsigned)((H + TT - 1) / TT), (unsigned)batch);
-  void (*k)(const T *, const T *, int64_t, const T *, int64_t, T *, int64_t, T *, int64_t, int, int, int, int);
-  if (op == DILATE) k = conn == 8 ? seg_backward<T, DILATE, 8, TT, kSeg> : seg_backward<T, DILATE, 4, TT, kSeg>;
-  else k = conn == 8 ? seg_backward<T, ERODE, 8, TT, kSeg> : seg_backward<T, ERODE, 4, TT, kSeg>;
-  if (cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::smem) !=
+  void (*ka)(const T *, const T *, int64_t, uint32_t *, T *, int, int, int);
+  if (op == DILATE) ka = conn == 8 ? seg_codes<T, DILATE, 8, TT, kSeg> : seg_codes<T, DILATE, 4, TT, kSeg>;
+  else ka = conn == 8 ? seg_codes<T, ERODE, 8, TT, kSeg> : seg_codes<T, ERODE, 4, TT, kSeg>;
+  if (cudaFuncSetAttribute((const void *)ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::a_smem) !=
       cudaSuccess)
     return GEO_ERR_CUDA;
-  k<<<grid, dim3(kSegT, kSegT), Gm::smem, s>>>(f0, mask, mpitch, gin, gi_pitch, gout, go_pitch, gm, gm_pitch, H, W, S,
-                                                 first);
+  ka<<<grid, kSplitThreads, Gm::a_smem, s>>>(f0, mask, mpitch, codes, f_next, H, W, S);
+  return cudaGetLastError() == cudaSuccess ? GEO_OK : GEO_ERR_CUDA;
+}
+
+template <typename T, int TT>
+int launch_gather(int conn, const uint32_t *codes, const T *gin, int64_t gi_pitch, T *gout, int64_t go_pitch, T *gm,
+                  int64_t gm_pitch, int H, int W, int batch, int S, int first, cudaStream_t s) {
+  using Gm = SplitGeom<T, TT, kSeg>;
+  const dim3 grid((unsigned)((W + TT - 1) / TT), (unsigned)((H + TT - 1) / TT), (unsigned)batch);
+  void (*kb)(const uint32_t *, const T *, int64_t, T *, int64_t, T *, int64_t, int, int, int, int) =
+      conn == 8 ? seg_gather<T, 8, TT, kSeg> : seg_gather<T, 4, TT, kSeg>;
+  if (cudaFuncSetAttribute((const void *)kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::b_smem) !=
+      cudaSuccess)
+    return GEO_ERR_CUDA;
+  kb<<<grid, kSplitThreads, Gm::b_smem, s>>>(codes, gin, gi_pitch, gout, go_pitch, gm, gm_pitch, H, W, S, first);
   return cudaGetLastError() == cudaSuccess ? GEO_OK : GEO_ERR_CUDA;
 }
 
@@ -386,16 +476,11 @@ int backward_impl(int dt, int op, int conn, const T *mask, const T *grad_out, T 
     return cudaGetLastError() == cudaSuccess ? GEO_OK : GEO_ERR_CUDA;
   }
   char *w = const_cast<char *>(ws);
-  // the sub-checkpoints come from the chain kernel, which takes one row
-  // stride for all planes: keep a packed copy of the mask
-  T *pmask = (T *)(w + Lw.off_state0);
-  if (cudaMemcpy2DAsync(pmask, W64 * sizeof(T), mask, pitch * sizeof(T), W64 * sizeof(T), H64 * (int64_t)batch,
-                        cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-    return GEO_ERR_CUDA;
   T *gbuf[2] = {(T *)(w + Lw.off_g0), (T *)(w + Lw.off_g1)};
   const T *gcur = grad_out;  // the gradient being propagated and its row stride
   int64_t gcur_pitch = pitch;
   int gsel = 0;
+  const size_t cst = (((size_t)Lw.npx * sizeof(uint32_t)) + 255) & ~(size_t)255;
   for (int64_t seg = Lw.nseg - 1; seg >= 0; --seg) {
     const int64_t t0 = seg * C;
     const int64_t t1 = (t0 + C < steps) ? t0 + C : steps;
@@ -404,12 +489,16 @@ int backward_impl(int dt, int op, int conn, const T *mask, const T *grad_out, T 
     const T *sub[64];
     if (nsub > 64) return GEO_ERR_ARG;
     sub[0] = (const T *)(w + Lw.off_ckpt + (size_t)seg * st);
-    for (int64_t i = 1; i < nsub; ++i) {
-      T *dst = (T *)(w + Lw.off_sub + (size_t)(i - 1) * st);
-      const int rc = run_chain(dt, sub[i - 1], pmask, dst, H64, W64, W64, conn, op, MODE_CHAIN, kSeg, nullptr, s,
-                               batch);
+    // forward over the segment: each code pass writes its sub-segment's
+    // code words and the next sub-segment's start state
+    for (int64_t i = 0; i < nsub; ++i) {
+      const int64_t a = t0 + i * kSeg;
+      const int S = (int)((a + kSeg < t1) ? kSeg : t1 - a);
+      T *next = (i + 1 < nsub) ? (T *)(w + Lw.off_sub + (size_t)i * st) : nullptr;
+      const int rc = launch_codes<T, TT>(op, conn, sub[i], mask, pitch, (uint32_t *)(w + Lw.off_codes + i * cst),
+                                         next, H, W, batch, S, s);
       if (rc != GEO_OK) return rc;
-      sub[i] = dst;
+      if (next) sub[i + 1] = next;
     }
     for (int64_t i = nsub - 1; i >= 0; --i) {
       const int64_t a = t0 + i * kSeg;
@@ -425,8 +514,8 @@ int backward_impl(int dt, int op, int conn, const T *mask, const T *grad_out, T 
         gsel ^= 1;
       }
       const int first = (a + S == steps);
-      const int rc = launch_seg<T, TT>(op, conn, sub[i], mask, pitch, gcur, gcur_pitch, gnext, gnext_pitch, grad_mask,
-                                       pitch, H, W, batch, S, first, s);
+      const int rc = launch_gather<T, TT>(conn, (const uint32_t *)(w + Lw.off_codes + i * cst), gcur, gcur_pitch,
+                                          gnext, gnext_pitch, grad_mask, pitch, H, W, batch, S, first, s);
       if (rc != GEO_OK) return rc;
       gcur = gnext;
       gcur_pitch = gnext_pitch;
