@@ -217,18 +217,21 @@ static int occupancy_rr(int dt, int op, int conn, int *bps, int variant = 0) {
 // one region-step (one step of one CTA on its whole region): a pass costs
 // kSyncSteps for its load / store / grid barrier, and every step costs one
 // unit per tile an SM has to process in that pass.
+PlanOverride &plan_override() {
+  thread_local PlanOverride o{0, -1};
+  return o;
+}
+
+// forceK > 0: that pass length (an override or the tune table), else the
+// cost model's choice
 static int plan_rr_uncached(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps_hint, int nsm, Plan *P,
-                            int batch, int tunedK, int variant) {
+                            int batch, int forceK, int variant) {
   const RRGeom g = rr_geom(dt, variant);
   const int RWID = 32 * g.CW, RHGT = g.NW * g.RW * g.B;
   int bps = 0;
   if (occupancy_rr(dt, op, conn, &bps, variant) != GEO_OK || bps <= 0) return GEO_ERR_CUDA;
   double kSyncSteps = 10.0;
   if (const char *e = getenv("GEOMORPH_SYNC")) kSyncSteps = atof(e);
-  // K fixed by the GEOMORPH_K override, else by the tune cache, else chosen
-  // by the cost model below
-  int forceK = tunedK;
-  if (const char *e = getenv("GEOMORPH_K")) forceK = atoi(e);
   double best = 1e300;
   Plan bp{};
   // K <= min(TH, TW): a tile's halo then reaches only its 8 neighbours,
@@ -269,7 +272,7 @@ static int plan_rr_uncached(int dt, int op, int conn, int64_t H, int64_t W, int6
   return GEO_OK;
 }
 
-using RRPlanKey = std::tuple<int, int, int, int, int, int64_t, int64_t, int64_t, int, std::string, std::string, int>;
+using RRPlanKey = std::tuple<int, int, int, int, int, int64_t, int64_t, int64_t, int, std::string, int, int>;
 static std::map<RRPlanKey, Plan> g_rr_plans;
 
 // code: the operation as a geo_item.op code (0..5), for the tune cache.
@@ -281,22 +284,28 @@ static int make_plan_rr(int dt, int op, int code, int conn, int64_t H, int64_t W
                         Plan *P, int batch, bool variants = false) {
   int dev = 0;
   cudaGetDevice(&dev);
-  const char *ek = getenv("GEOMORPH_K");
   const char *es = getenv("GEOMORPH_SYNC");
+  // the pass length and shape: the autotuner's per-thread override, else the
+  // GEOMORPH_K / GEOMORPH_VARIANT environment overrides (sweeps), else the
+  // tune table, else the cost model (K = 0) in the default shape
+  const PlanOverride &ov = plan_override();
+  const char *ek = getenv("GEOMORPH_K");
   const char *ev = getenv("GEOMORPH_VARIANT");
+  const int oK = ov.K > 0 ? ov.K : (ek ? atoi(ek) : 0);
+  const int oV = ov.variant >= 0 ? ov.variant : (ev ? atoi(ev) : -1);
   int tk = 0, tv = 0;
-  if (variants && ev) {
-    // variant override (the autotuner's sweep); K from GEOMORPH_K or the cost model
-    tv = atoi(ev);
-    if (tv < 0 || tv >= rr_variants(dt)) return GEO_ERR_ARG;
-  } else if (!ek) {
-    if (variants && batch == 1) {
-      if (!tuned_plan(dt, code, conn, H, W, steps_hint, &tk, &tv) || tv < 0 || tv >= rr_variants(dt)) tk = tv = 0;
-    } else {
-      tk = tuned_k(dt, code, conn, H, W, steps_hint);
-    }
+  if (variants && oV >= 0) {
+    tk = oK;
+    tv = oV;
+    if (tv >= rr_variants(dt)) return GEO_ERR_ARG;
+  } else if (oK > 0) {
+    tk = oK;
+  } else if (variants && batch == 1) {
+    if (!tuned_plan(dt, code, conn, H, W, steps_hint, &tk, &tv) || tv < 0 || tv >= rr_variants(dt)) tk = tv = 0;
+  } else {
+    tk = tuned_k(dt, code, conn, H, W, steps_hint);
   }
-  RRPlanKey key{dev, batch, dt, op, conn, H, W, steps_hint, nsm, ek ? ek : "", es ? es : "", tk * 16 + tv};
+  RRPlanKey key{dev, batch, dt, op, conn, H, W, steps_hint, nsm, es ? es : "", tk, tv};
   {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     auto it = g_rr_plans.find(key);

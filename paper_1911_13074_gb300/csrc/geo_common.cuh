@@ -138,6 +138,14 @@ inline bool single_tile(const Plan &P, int batch) { return batch <= 1 && P.tiles
 // as geo_item.op), or 0 when the tune cache has no entry (geo_tune.cu). The
 // entry of the exact (H, W) is used first, else that of its size class.
 int tuned_k(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps);
+// The autotuner's planner override for the calling thread (geo_tune.cu sets
+// it around each timed call, so tuning never touches the process
+// environment): K > 0 forces the pass length, variant >= 0 the shape variant
+// of the register kernel; {0, -1} = none (geo_api.cu).
+struct PlanOverride {
+  int K, variant;
+};
+PlanOverride &plan_override();
 // Tuned (K, variant) over every kernel shape; false when there is no entry.
 bool tuned_plan(int dt, int op, int conn, int64_t H, int64_t W, int64_t steps, int *K, int *variant);
 // The batch planner's per-pass charge chosen by geo_batch_autotune (10 when

@@ -202,14 +202,10 @@ using namespace geo;
 
 namespace {
 
-// Time one item with K and the shape variant forced through the planner
-// overrides (GEOMORPH_K, GEOMORPH_VARIANT); returns ms per run.
+// Time one item with K and the shape variant forced through the calling
+// thread's planner override; returns ms per run.
 float time_item(const geo_item &x, int K, int variant, int reps, cudaStream_t s, int *rc_out) {
-  char kbuf[32], vbuf[32];
-  snprintf(kbuf, sizeof kbuf, "%d", K);
-  snprintf(vbuf, sizeof vbuf, "%d", variant);
-  setenv("GEOMORPH_K", kbuf, 1);
-  setenv("GEOMORPH_VARIANT", vbuf, 1);
+  plan_override() = PlanOverride{K, variant};
   auto once = [&]() -> int {
     switch (x.op) {
       case 0: return geo_dilate_chain(x.dtype, x.marker, x.mask, x.out, x.height, x.width, x.pitch, x.conn, x.steps, s);
@@ -234,8 +230,7 @@ float time_item(const geo_item &x, int K, int variant, int reps, cudaStream_t s,
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  unsetenv("GEOMORPH_K");
-  unsetenv("GEOMORPH_VARIANT");
+  plan_override() = PlanOverride{0, -1};
   *rc_out = rc;
   return reps > 0 ? ms / reps : ms;
 }
