@@ -63,9 +63,9 @@ __device__ __forceinline__ bool prog_tile(const TileLaunch &L, const Plane &src,
   }
   if (!loaded) R::load_words(src, L.H, L.W, gy0, gx, src_cg, false, w);
   R::load_words(src, L.H, L.W, gy0, gx, false, true, m);  // the virtual mask of this operation
-  // tagged hand-over: the loads of the pass before any store of the CTA
-  // (the same write-after-read argument as in rr_kernel)
-  if constexpr (TAG) fence_acq_rel_gpu();
+  // tagged hand-over: no fence between the pass's loads and its stores, by
+  // the same write-after-read argument as in rr_kernel (every store of a
+  // pass depends on that pass's tag checks)
   for (int j = 0; j < S; ++j) {
     ok &= R::template step<8>(w, m, xb0 + (size_t)parity * xb_stride, bar, parity, lane, warp);
     parity ^= 1;
