@@ -12,25 +12,40 @@
 //
 //   keys    order-preserving 64-bit keys of marker and mask (the int64 key of
 //           the float64 path with the sign bit flipped, so that unsigned order
-//           is numeric order; -0.0 sorts below +0.0, as there)
-//   sort    least-significant-digit radix sort, 8 passes of 8 bits: per block
-//           digit histogram, one scan, stable scatter (warps rank equal
-//           digits with __match_any_sync, in key order)
-//   unique  flags where a key differs from its predecessor, scan, compact
-//   map     rank of each pixel by binary search among the distinct keys
+//           is numeric order; -0.0 sorts below +0.0, as there), each with its
+//           position, and in the same pass the global histograms of all
+//           eight 8-bit digits
+//   sort    least-significant-digit radix sort of (key, position), 8 passes
+//           of one kernel each: a block takes the next tile by ticket, ranks
+//           its keys by digit in position order (warps group equal digits
+//           by one shared-memory bit per lane), publishes its digit counts
+//           and finds the
+//           counts of the tiles before it by decoupled look-back (bounded
+//           waits), orders the tile by digit in shared memory and writes
+//           each digit's run where the global histogram and the look-back
+//           put it
+//   unique  flags where a key differs from its predecessor, one scan: the
+//           rank of every sorted key; the distinct keys compacted and every
+//           rank written back to its pixel's position
 //   chain   float32 chain / window / reconstruction on the ranks
 //   unmap   out = the distinct key at the result's rank, as float64
 #include <cstdlib>
 #include <cstring>
 
 #include "geo_common.cuh"
+#include "geo_tile.cuh"
 
 namespace geo {
 namespace {
 
-constexpr int kRsThreads = 256, kRsItems = 16, kRsTile = kRsThreads * kRsItems;  // 4096 keys per block
-constexpr int kRsWarps = kRsThreads / 32, kRsWarpKeys = kRsTile / kRsWarps;      // 512 keys per warp
+constexpr int kOsThreads = 256, kOsWarps = kOsThreads / 32;
+constexpr int kOsTile = 4096, kOsWarpKeys = kOsTile / kOsWarps;  // keys per tile, per warp
+constexpr int kDigits = 256, kPasses = 8;
 constexpr int kScanThreads = 1024, kScanItems = 4, kScanTile = kScanThreads * kScanItems;
+// look-back word of one tile and digit: bits 31..30 0 = not yet published,
+// 1 = the tile's own count, 2 = inclusive count of all tiles up to it;
+// bits 29..0 the count (at most 2^25 keys)
+constexpr uint32_t kLbAgg = 1u << 30, kLbPre = 2u << 30, kLbCount = (1u << 30) - 1u;
 
 __device__ __forceinline__ uint64_t dkey(double d) {
   const long long b = __double_as_longlong(d);
@@ -42,31 +57,46 @@ __device__ __forceinline__ double kdouble(uint64_t u) {
   return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
 }
 
-// keys[0 .. H*W) = marker, keys[H*W .. 2 H*W) = mask (when given)
-__global__ void rk_keys(const double *__restrict__ a, const double *__restrict__ b, int64_t H, int64_t W,
-                        int64_t pitch, uint64_t *__restrict__ keys) {
-  const int64_t n = H * W;
+// keys[0 .. H*W) = marker, keys[H*W .. 2 H*W) = mask (when given), pos[i] =
+// i, and hist[p * 256 + d] += the keys whose digit p (bits 8p .. 8p + 7) is d
+__global__ void __launch_bounds__(256) rk_keys(const double *__restrict__ a, const double *__restrict__ b, int64_t H,
+                                               int64_t W, int64_t pitch, uint64_t *__restrict__ keys,
+                                               uint32_t *__restrict__ pos, uint32_t *__restrict__ hist) {
+  __shared__ uint32_t h[kPasses * kDigits];
+  for (int i = threadIdx.x; i < kPasses * kDigits; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const int64_t npx = H * W, n = b ? 2 * npx : npx;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t y = i / W, x = i - y * W;
-    keys[i] = dkey(a[y * pitch + x]);
-    if (b) keys[n + i] = dkey(b[y * pitch + x]);
+    const int64_t j = i < npx ? i : i - npx;
+    const int64_t y = j / W, x = j - y * W;
+    const uint64_t k = dkey(i < npx ? a[y * pitch + x] : b[y * pitch + x]);
+    keys[i] = k;
+    pos[i] = (uint32_t)i;
+#pragma unroll
+    for (int p = 0; p < kPasses; ++p) atomicAdd(&h[p * kDigits + (int)((k >> (8 * p)) & 255u)], 1u);
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kPasses * kDigits; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], h[i]);
 }
 
-// per-block histogram of one digit: hist[digit * nblocks + block]
-__global__ void __launch_bounds__(kRsThreads) rk_hist(const uint64_t *__restrict__ keys, int64_t n, int shift,
-                                                      uint32_t *__restrict__ hist, int nblocks) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * kRsTile;
-#pragma unroll 4
-  for (int i = threadIdx.x; i < kRsTile; i += kRsThreads) {
-    const int64_t idx = base + i;
-    if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+// hist[p][d] -> exclusive prefix over d (the first output position of digit
+// d in pass p); one block of 256 threads
+__global__ void __launch_bounds__(kDigits) rk_digit_offsets(uint32_t *__restrict__ hist) {
+  __shared__ uint32_t v[kDigits];
+  for (int p = 0; p < kPasses; ++p) {
+    const uint32_t c = hist[p * kDigits + threadIdx.x];
+    v[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 1; o < kDigits; o <<= 1) {
+      const uint32_t t = threadIdx.x >= (unsigned)o ? v[threadIdx.x - o] : 0u;
+      __syncthreads();
+      v[threadIdx.x] += t;
+      __syncthreads();
+    }
+    hist[p * kDigits + threadIdx.x] = v[threadIdx.x] - c;
+    __syncthreads();
   }
-  __syncthreads();
-  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
 // Exclusive scan of n uint32 in place, one block, in chunks of kScanTile
@@ -108,52 +138,185 @@ __global__ void __launch_bounds__(kScanThreads) rk_scan_small(uint32_t *__restri
   if (total && threadIdx.x == 0) *total = carry_s;
 }
 
-// Stable scatter of one digit. Warp w of a block owns keys [w * 512, (w + 1)
-// * 512) of the block's tile and walks them in rounds of 32 in key order:
-// first counting each digit, then placing each key at the block's offset of
-// its digit + the counts of earlier warps + the keys of its digit seen
-// earlier in the warp + the lanes below it in the round with the same digit.
-__global__ void __launch_bounds__(kRsThreads) rk_scatter(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
-                                                         int64_t n, int shift, const uint32_t *__restrict__ hist,
-                                                         int nblocks) {
-  __shared__ uint32_t cnt[kRsWarps][256];
-  __shared__ uint32_t base_s[256];
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// One pass of the radix sort of (key, pos) on the digit at `shift`.
+// A block takes tile t by ticket (so every tile before t belongs to a block
+// that is already running: the look-back waits always end), and warp w owns
+// keys [w * 512, (w + 1) * 512) of the tile, 16 per lane held in registers
+// and walked in rounds of 32 in position order (warp_digit_peers groups the
+// lanes of equal digits): first counting each digit, then placing each key in
+// shared memory at the tile's start of its digit + the counts of earlier
+// warps + the keys of its digit seen earlier in the warp + the lanes below
+// it in the round with the same digit (a stable local sort by digit). The
+// tile's digit counts are published before that placement and the tiles
+// before it are looked up after it (decoupled look-back over per-tile,
+// per-digit words: a tile's own count, or the inclusive count once the tile
+// knows it; each lane reads kLbWindow predecessors at once), so that the
+// counts of most earlier tiles are there when needed. Digit d's keys of the
+// tile then go, contiguously, to doff[d] + the sum found. A look-back wait
+// that expires (limit_ns) records GEO_ERR_TIMEOUT and the block writes
+// nothing.
+constexpr int kLbWindow = 32;
+constexpr int kOsRounds = kOsWarpKeys / 32;  // keys per lane
+
+// The lanes of the warp whose digit equals this lane's (d < 256; a lane with
+// d >= 256 has no peers): each lane sets its bit in the warp's word of its
+// digit, reads the word back, and the lowest lane of each group clears it
+// for the next round. (__match_any_sync gives the same masks, but measured
+// about 1000 SM clocks a call with some 30 distinct digits among 32 lanes.)
+__device__ __forceinline__ unsigned warp_digit_peers(uint32_t *wm, unsigned d, int lane) {
+  const unsigned me = 1u << lane;
+  if (d < 256u) atomicOr(&wm[d], me);
+  __syncwarp();
+  const unsigned peers = d < 256u ? wm[d] : me;
+  __syncwarp();
+  if (d < 256u && (peers & (me - 1u)) == 0) wm[d] = 0;
+  __syncwarp();
+  return peers;
+}
+__global__ void __launch_bounds__(kOsThreads) rk_onesweep(const uint64_t *__restrict__ kin,
+                                                          const uint32_t *__restrict__ pin, uint64_t *__restrict__ kout,
+                                                          uint32_t *__restrict__ pout, int64_t n, int shift,
+                                                          const uint32_t *__restrict__ doff, uint32_t *lookback,
+                                                          uint32_t *ticket, int *status,
+                                                          unsigned long long limit_ns) {
+  extern __shared__ __align__(16) char os_dyn[];
+  uint64_t *sk = reinterpret_cast<uint64_t *>(os_dyn);               // the tile's keys, by digit
+  uint32_t *sp = reinterpret_cast<uint32_t *>(os_dyn + 8 * kOsTile);  // and their positions
+  __shared__ uint32_t cnt[kOsWarps][kDigits];
+  __shared__ uint32_t wmask[kOsWarps][kDigits];  // warp_digit_peers' words
+  __shared__ uint32_t dend[kDigits], tcnt[kDigits], gbase[kDigits];
+  __shared__ int tile_s, fail_s;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&cnt[0][0])[i] = 0;
-  base_s[threadIdx.x] = hist[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+  if (threadIdx.x == 0) {
+    tile_s = (int)atomicAdd(ticket, 1u);
+    fail_s = 0;
+  }
+  for (int i = threadIdx.x; i < kOsWarps * kDigits; i += kOsThreads) {
+    (&cnt[0][0])[i] = 0;
+    (&wmask[0][0])[i] = 0;
+  }
   __syncthreads();
-  const int64_t wbase = (int64_t)blockIdx.x * kRsTile + (int64_t)warp * kRsWarpKeys;
+  const int tile = tile_s;
+  const int64_t wbase = (int64_t)tile * kOsTile + (int64_t)warp * kOsWarpKeys;
   const unsigned lt = (1u << lane) - 1u;
-  for (int r = 0; r < kRsWarpKeys; r += 32) {
-    const int64_t idx = wbase + r + lane;
-    const unsigned d = idx < n ? (unsigned)((in[idx] >> shift) & 255u) : 256u + lane;  // past the end: no peers
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
+  // the lane's keys of every round, all loads in flight together
+  uint64_t k[kOsRounds];
+  uint32_t pk[kOsRounds];
+#pragma unroll
+  for (int r = 0; r < kOsRounds; ++r) {
+    const int64_t idx = wbase + 32 * r + lane;
+    k[r] = idx < n ? kin[idx] : 0ull;
+    pk[r] = idx < n ? pin[idx] : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < kOsRounds; ++r) {
+    const int64_t idx = wbase + 32 * r + lane;
+    const unsigned d = idx < n ? (unsigned)((k[r] >> shift) & 255u) : 256u;  // past the end: no peers
+    const unsigned peers = warp_digit_peers(wmask[warp], d, lane);
     if (d < 256u && (peers & lt) == 0) cnt[warp][d] += __popc(peers);
     __syncwarp();
   }
   __syncthreads();
-  // per digit: exclusive prefix over the warps, then the block's offset
   {
-    const int d = threadIdx.x;  // 256 threads, one per digit
-    uint32_t run = base_s[d];
+    const int d = threadIdx.x;  // one thread per digit
+    uint32_t c = 0;
 #pragma unroll
-    for (int w = 0; w < kRsWarps; ++w) {
-      const uint32_t c = cnt[w][d];
-      cnt[w][d] = run;
-      run += c;
+    for (int w = 0; w < kOsWarps; ++w) {
+      const uint32_t x = cnt[w][d];
+      cnt[w][d] = c;  // the warp's start within the digit's keys of this tile
+      c += x;
     }
+    tcnt[d] = c;
+    dend[d] = c;
+    st_relaxed_u32(lookback + (int64_t)tile * kDigits + d, (tile == 0 ? kLbPre : kLbAgg) | c);
   }
   __syncthreads();
-  for (int r = 0; r < kRsWarpKeys; r += 32) {
-    const int64_t idx = wbase + r + lane;
+  for (int o = 1; o < kDigits; o <<= 1) {  // dend[d]: the tile's keys of digits <= d
+    const uint32_t t = threadIdx.x >= (unsigned)o ? dend[threadIdx.x - o] : 0u;
+    __syncthreads();
+    dend[threadIdx.x] += t;
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < kOsRounds; ++r) {
+    const int64_t idx = wbase + 32 * r + lane;
     const bool valid = idx < n;
-    const uint64_t k = valid ? in[idx] : 0ull;
-    const unsigned d = valid ? (unsigned)((k >> shift) & 255u) : 256u + lane;
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
-    if (valid) out[cnt[warp][d] + __popc(peers & lt)] = k;
+    const unsigned d = valid ? (unsigned)((k[r] >> shift) & 255u) : 256u;
+    const unsigned peers = warp_digit_peers(wmask[warp], d, lane);
+    if (valid) {
+      const uint32_t at = (d == 0 ? 0u : dend[d - 1]) + cnt[warp][d] + __popc(peers & lt);
+      sk[at] = k[r];
+      sp[at] = pk[r];
+    }
     __syncwarp();
     if (valid && (peers & lt) == 0) cnt[warp][d] += __popc(peers);
     __syncwarp();
+  }
+  {
+    // look-back for digit d over the tiles before this one, kLbWindow at a time
+    const int d = threadIdx.x;
+    uint32_t before = 0;
+    if (tile > 0) {
+      unsigned long long t0 = 0;
+      unsigned spins = 0;
+      int j = tile - 1;
+      bool done = false;
+      while (!done) {
+        uint32_t wv[kLbWindow];
+#pragma unroll
+        for (int q = 0; q < kLbWindow; ++q)
+          wv[q] = (j - q >= 0) ? ld_relaxed_u32(lookback + (int64_t)(j - q) * kDigits + d) : kLbPre;
+        // nearest first: add counts until an inclusive one; stop at the first unpublished word
+        int q = 0;
+        for (; q < kLbWindow && j - q >= 0; ++q) {
+          const uint32_t w = wv[q];
+          if ((w >> 30) == 0u) break;
+          before += w & kLbCount;
+          if ((w >> 30) == 2u) {
+            done = true;
+            break;
+          }
+        }
+        if (done) break;
+        if (q == 0) {  // the nearest word not published yet: wait (bounded)
+          if (spins == 0) t0 = globaltimer_ns();
+          if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > limit_ns) {
+            fail_s = 1;
+            break;
+          }
+          continue;
+        }
+        j -= q;
+        if (j < 0) break;  // cannot happen: tile 0's word is inclusive
+      }
+      st_relaxed_u32(lookback + (int64_t)tile * kDigits + d, kLbPre | (before + tcnt[d]));
+    }
+    gbase[d] = doff[d] + before;
+  }
+  __syncthreads();
+  if (fail_s) {
+    if (threadIdx.x == 0) record_status(status, GEO_ERR_TIMEOUT);
+    return;
+  }
+  const int64_t t0 = (int64_t)tile * kOsTile;
+  const int tn = (int)((n - t0) < kOsTile ? (n - t0) : kOsTile);
+  for (int i = threadIdx.x; i < tn; i += kOsThreads) {
+    const uint64_t k = sk[i];
+    const unsigned d = (unsigned)((k >> shift) & 255u);
+    const int64_t o = (int64_t)gbase[d] + (i - (int64_t)(d == 0 ? 0u : dend[d - 1]));
+    if (o >= 0 && o < n) {
+      kout[o] = k;
+      pout[o] = sp[i];
+    }
   }
 }
 
@@ -199,48 +362,19 @@ __global__ void rk_scan_add(uint32_t *__restrict__ v, int64_t n, const uint32_t 
   if (idx < n) v[idx] += sums[idx / kScanTile];
 }
 
-// compact the run starts: uniq[scan[i]] = sorted[i] where flags[i]
-__global__ void rk_compact(const uint64_t *__restrict__ s, const uint32_t *__restrict__ flags_scan, int64_t n,
-                           uint64_t *__restrict__ uniq) {
+// After the scan of the run-start flags (exclusive): the rank of sorted key i
+// among the distinct keys is scan[i] + flag[i] - 1. The run starts go to
+// uniq[rank], and every rank to the key's position: ranks[pos[i]] (marker
+// then mask, as the keys were laid out).
+__global__ void rk_finish(const uint64_t *__restrict__ s, const uint32_t *__restrict__ pos,
+                          const uint32_t *__restrict__ flags_scan, int64_t n, uint64_t *__restrict__ uniq,
+                          float *__restrict__ ranks) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    if (i == 0 || s[i] != s[i - 1]) uniq[flags_scan[i]] = s[i];
-  }
-}
-
-// Bucket table of the distinct keys by their top kPrefixBits: the keys with
-// prefix p are uniq[start[p] .. end[p]). Only prefixes that occur are
-// written, and only those are read (every looked-up key is present).
-constexpr int kPrefixBits = 20;
-__device__ __forceinline__ uint32_t key_prefix(uint64_t k) { return (uint32_t)(k >> (64 - kPrefixBits)); }
-
-__global__ void rk_buckets(const uint64_t *__restrict__ uniq, const uint32_t *__restrict__ U, int64_t n,
-                           uint32_t *__restrict__ start, uint32_t *__restrict__ end) {
-  const int64_t u = *U;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n && i < u;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t p = key_prefix(uniq[i]);
-    if (i == 0 || key_prefix(uniq[i - 1]) != p) start[p] = (uint32_t)i;
-    if (i == u - 1 || key_prefix(uniq[i + 1]) != p) end[p] = (uint32_t)(i + 1);
-  }
-}
-
-// ranks (as float32) of an image's values among the distinct keys: binary
-// search inside the key's prefix bucket
-__global__ void rk_map(const double *__restrict__ a, int64_t H, int64_t W, int64_t pitch,
-                       const uint64_t *__restrict__ uniq, const uint32_t *__restrict__ start,
-                       const uint32_t *__restrict__ end, float *__restrict__ r) {
-  const int64_t n = H * W;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t y = i / W, x = i - y * W;
-    const uint64_t k = dkey(a[y * pitch + x]);
-    const uint32_t p = key_prefix(k);
-    uint32_t lo = start[p], hi = end[p];  // first index with uniq >= k (the key is present)
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (uniq[mid] < k) lo = mid + 1;
-      else hi = mid;
-    }
-    r[i] = (float)lo;
+    const uint64_t k = s[i];
+    const bool start = (i == 0 || k != s[i - 1]);
+    const uint32_t r = flags_scan[i] + (start ? 1u : 0u) - 1u;
+    if (start) uniq[r] = k;
+    ranks[pos[i]] = (float)r;
   }
 }
 
@@ -290,45 +424,75 @@ int run_chain_ranked(const double *marker, const double *mask, double *out, int6
                      int conn, int op, int mode, int64_t steps, int64_t *steps_out, void *stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t npx = H * W, n = npx * (mask ? 2 : 1);
-  const int nblocks = (int)((n + kRsTile - 1) / kRsTile);
+  const int ntiles = (int)((n + kOsTile - 1) / kOsTile);
   const int64_t nsb = (n + kScanTile - 1) / kScanTile;
-  // scratch: [keys A][keys B][uniq][flags/scan][hist][scan block sums][U][ranks: marker, mask, out]
-  //          [bucket start][bucket end]
-  const size_t kb = up256((size_t)n * 8), fb = up256((size_t)n * 4), hb = up256((size_t)256 * nblocks * 4);
-  const size_t sb = up256((size_t)(nsb > 0 ? nsb : 1) * 4), rb = up256((size_t)npx * 4);
-  const size_t tb = (size_t)4 << kPrefixBits;
-  const size_t total = 3 * kb + fb + hb + sb + 256 + 3 * rb + 2 * tb;
+  // scratch: [keys A][keys B][pos A][pos B][uniq][flags/scan][digit offsets][scan block sums][U]
+  //          [tickets][look-back words, per pass][ranks: marker, mask][ranks out]
+  const size_t kb = up256((size_t)n * 8), pb = up256((size_t)n * 4), fb = up256((size_t)n * 4);
+  const size_t hb = up256((size_t)kPasses * kDigits * 4), sb = up256((size_t)(nsb > 0 ? nsb : 1) * 4);
+  const size_t lbb = up256((size_t)kPasses * ntiles * kDigits * 4), rb = up256((size_t)npx * 4);
+  const size_t total = 3 * kb + 2 * pb + fb + hb + sb + 256 + 256 + lbb + 3 * rb;
   void *scratch = nullptr;
   int rc = pool_alloc(&scratch, total, s);
   if (rc != GEO_OK) return rc;
+  int *status = nullptr;
+  if (device_status_word(&status) != GEO_OK) {
+    pool_free(scratch, s);
+    return GEO_ERR_CUDA;
+  }
   char *p = (char *)scratch;
   uint64_t *ka = (uint64_t *)p, *kbuf = (uint64_t *)(p + kb), *uniq = (uint64_t *)(p + 2 * kb);
-  uint32_t *flags = (uint32_t *)(p + 3 * kb), *hist = (uint32_t *)(p + 3 * kb + fb);
-  uint32_t *bsums = (uint32_t *)(p + 3 * kb + fb + hb), *U = (uint32_t *)(p + 3 * kb + fb + hb + sb);
-  float *rm = (float *)(p + 3 * kb + fb + hb + sb + 256), *rk = (float *)((char *)rm + rb);
-  float *ro = (float *)((char *)rm + 2 * rb);
-  uint32_t *bstart = (uint32_t *)((char *)rm + 3 * rb), *bend = (uint32_t *)((char *)rm + 3 * rb + tb);
+  p += 3 * kb;
+  uint32_t *pa = (uint32_t *)p, *pbuf = (uint32_t *)(p + pb);
+  p += 2 * pb;
+  uint32_t *flags = (uint32_t *)p;
+  p += fb;
+  uint32_t *hist = (uint32_t *)p;  // digit histograms, then offsets; zeroed with the tickets and look-back
+  p += hb;
+  uint32_t *bsums = (uint32_t *)p;
+  p += sb;
+  uint32_t *U = (uint32_t *)p;
+  p += 256;
+  uint32_t *tickets = (uint32_t *)p;
+  uint32_t *lookback = (uint32_t *)(p + 256);
+  p += 256 + lbb;
+  float *rm = (float *)p, *rk = (float *)(p + (mask ? (size_t)npx * 4 : 0)), *ro = (float *)(p + 2 * rb);
+  // (marker and mask ranks contiguous: ranks[pos] with pos < npx the marker's)
 
-  rk_keys<<<ew_grid(npx), 256, 0, s>>>(marker, mask, H, W, pitch, ka);
-  uint64_t *src = ka, *dst = kbuf;
-  for (int shift = 0; shift < 64; shift += 8) {
-    rk_hist<<<nblocks, kRsThreads, 0, s>>>(src, n, shift, hist, nblocks);
-    if (scan_u32(hist, (int64_t)256 * nblocks, bsums, nullptr, s) != GEO_OK) rc = GEO_ERR_CUDA;
-    rk_scatter<<<nblocks, kRsThreads, 0, s>>>(src, dst, n, shift, hist, nblocks);
-    uint64_t *t = src;
-    src = dst;
-    dst = t;
-  }
-  // 8 passes: the sorted keys are back in ka (src)
-  rk_flags<<<ew_grid(n), 256, 0, s>>>(src, n, flags);
-  if (cudaGetLastError() != cudaSuccess) rc = GEO_ERR_CUDA;
-  if (rc == GEO_OK) rc = scan_u32(flags, n, bsums, U, s);
+  if (cudaMemsetAsync(hist, 0, hb, s) != cudaSuccess ||
+      cudaMemsetAsync(tickets, 0, 256 + lbb, s) != cudaSuccess)
+    rc = GEO_ERR_CUDA;
+  // the one-sweep kernel's tile (keys and positions) takes 48 KB of dynamic
+  // shared memory next to its static counts
+  const int os_smem = kOsTile * (8 + 4);
+  if (cudaFuncSetAttribute(rk_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, os_smem) != cudaSuccess)
+    rc = GEO_ERR_CUDA;
+  const bool fault = host_fault() == FAULT_TIMEOUT;
+  const unsigned long long limit = fault ? kFaultWaitNs : kWaitLimitNs;
   if (rc == GEO_OK) {
-    rk_compact<<<ew_grid(n), 256, 0, s>>>(src, flags, n, uniq);
-    rk_buckets<<<ew_grid(n), 256, 0, s>>>(uniq, U, n, bstart, bend);
-    rk_map<<<ew_grid(npx), 256, 0, s>>>(marker, H, W, pitch, uniq, bstart, bend, rm);
-    if (mask) rk_map<<<ew_grid(npx), 256, 0, s>>>(mask, H, W, pitch, uniq, bstart, bend, rk);
+    rk_keys<<<ew_grid(n), 256, 0, s>>>(marker, mask, H, W, pitch, ka, pa, hist);
+    rk_digit_offsets<<<1, kDigits, 0, s>>>(hist);
+    uint64_t *ks = ka, *kd = kbuf;
+    uint32_t *ps = pa, *pd = pbuf;
+    for (int pass = 0; pass < kPasses; ++pass) {
+      rk_onesweep<<<ntiles, kOsThreads, os_smem, s>>>(ks, ps, kd, pd, n, 8 * pass, hist + pass * kDigits,
+                                                      lookback + (size_t)pass * ntiles * kDigits, tickets + pass,
+                                                      status, limit);
+      uint64_t *t = ks;
+      ks = kd;
+      kd = t;
+      uint32_t *u = ps;
+      ps = pd;
+      pd = u;
+    }
+    // 8 passes: the sorted keys and their positions are back in ka / pa (ks / ps)
+    rk_flags<<<ew_grid(n), 256, 0, s>>>(ks, n, flags);
     if (cudaGetLastError() != cudaSuccess) rc = GEO_ERR_CUDA;
+    if (rc == GEO_OK) rc = scan_u32(flags, n, bsums, U, s);
+    if (rc == GEO_OK) {
+      rk_finish<<<ew_grid(n), 256, 0, s>>>(ks, ps, flags, n, uniq, rm);
+      if (cudaGetLastError() != cudaSuccess) rc = GEO_ERR_CUDA;
+    }
   }
   if (rc == GEO_OK)
     rc = run_chain_any(GEO_F32, rm, mask ? rk : nullptr, ro, H, W, W, conn, op, mode, steps, steps_out, stream, 1);
