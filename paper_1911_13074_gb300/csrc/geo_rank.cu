@@ -182,7 +182,7 @@ __device__ __forceinline__ unsigned warp_digit_peers(uint32_t *wm, unsigned d, i
   __syncwarp();
   return peers;
 }
-__global__ void __launch_bounds__(kOsThreads) rk_onesweep(const uint64_t *__restrict__ kin,
+__global__ void __launch_bounds__(kOsThreads, 2) rk_onesweep(const uint64_t *__restrict__ kin,
                                                           const uint32_t *__restrict__ pin, uint64_t *__restrict__ kout,
                                                           uint32_t *__restrict__ pout, int64_t n, int shift,
                                                           const uint32_t *__restrict__ doff, uint32_t *lookback,
@@ -465,7 +465,9 @@ int run_chain_ranked(const double *marker, const double *mask, double *out, int6
   // the one-sweep kernel's tile (keys and positions) takes 48 KB of dynamic
   // shared memory next to its static counts
   const int os_smem = kOsTile * (8 + 4);
-  if (cudaFuncSetAttribute(rk_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, os_smem) != cudaSuccess)
+  if (cudaFuncSetAttribute(rk_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, os_smem) != cudaSuccess ||
+      cudaFuncSetAttribute(rk_onesweep, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared) != cudaSuccess)
     rc = GEO_ERR_CUDA;
   const bool fault = host_fault() == FAULT_TIMEOUT;
   const unsigned long long limit = fault ? kFaultWaitNs : kWaitLimitNs;
