@@ -39,7 +39,7 @@ namespace geo {
 namespace {
 
 constexpr int kOsThreads = 256, kOsWarps = kOsThreads / 32;
-constexpr int kOsTile = 4096, kOsWarpKeys = kOsTile / kOsWarps;  // keys per tile, per warp
+constexpr int kOsTile = 2048, kOsWarpKeys = kOsTile / kOsWarps;  // keys per tile, per warp
 constexpr int kDigits = 256, kPasses = 8;
 constexpr int kScanThreads = 1024, kScanItems = 4, kScanTile = kScanThreads * kScanItems;
 // look-back word of one tile and digit: bits 31..30 0 = not yet published,
@@ -150,7 +150,7 @@ __device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
 // One pass of the radix sort of (key, pos) on the digit at `shift`.
 // A block takes tile t by ticket (so every tile before t belongs to a block
 // that is already running: the look-back waits always end), and warp w owns
-// keys [w * 512, (w + 1) * 512) of the tile, 16 per lane held in registers
+// keys [w * 256, (w + 1) * 256) of the tile, 8 per lane held in registers
 // and walked in rounds of 32 in position order (warp_digit_peers groups the
 // lanes of equal digits): first counting each digit, then placing each key in
 // shared memory at the tile's start of its digit + the counts of earlier
@@ -164,7 +164,7 @@ __device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
 // tile then go, contiguously, to doff[d] + the sum found. A look-back wait
 // that expires (limit_ns) records GEO_ERR_TIMEOUT and the block writes
 // nothing.
-constexpr int kLbWindow = 32;
+constexpr int kLbWindow = 16;
 constexpr int kOsRounds = kOsWarpKeys / 32;  // keys per lane
 
 // The lanes of the warp whose digit equals this lane's (d < 256; a lane with
@@ -182,7 +182,7 @@ __device__ __forceinline__ unsigned warp_digit_peers(uint32_t *wm, unsigned d, i
   __syncwarp();
   return peers;
 }
-__global__ void __launch_bounds__(kOsThreads, 2) rk_onesweep(const uint64_t *__restrict__ kin,
+__global__ void __launch_bounds__(kOsThreads, 4) rk_onesweep(const uint64_t *__restrict__ kin,
                                                           const uint32_t *__restrict__ pin, uint64_t *__restrict__ kout,
                                                           uint32_t *__restrict__ pout, int64_t n, int shift,
                                                           const uint32_t *__restrict__ doff, uint32_t *lookback,
