@@ -412,12 +412,13 @@ bool rank_path_applies(int64_t H, int64_t W, bool has_mask, int mode, int64_t st
   const int64_t n = H * W * (has_mask ? 2 : 1);
   if (n > ((int64_t)1 << 24)) return false;  // ranks must stay exact float32 integers
   if (e && strcmp(e, "ranks") == 0) return true;
-  // The transform costs about 0.5 ms at 1024^2 (radix sort, ranks, map
-  // back), about 200 int64-key steps there; reconstruction takes its chain
-  // length from the image's longer side. Small images stay on the keys (the
-  // launches of the transform dominate there).
+  // The transform costs about 0.45 ms at 1024^2 (radix sort, ranks, map
+  // back); a step there takes about 3.8 us on int64 keys and 0.7 us on the
+  // ranks, so the ranks pay from about 150 steps on. Reconstruction takes
+  // its chain length from the image's longer side. Small images stay on the
+  // keys (the launches of the transform dominate there).
   const int64_t est = mode == MODE_REC ? (H > W ? H : W) : steps;
-  return est >= 256 && H * W >= ((int64_t)1 << 16);
+  return est >= 160 && H * W >= ((int64_t)1 << 16);
 }
 
 int run_chain_ranked(const double *marker, const double *mask, double *out, int64_t H, int64_t W, int64_t pitch,
