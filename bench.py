@@ -258,8 +258,8 @@ def dtype_fractions(sec, nsm, u8_rate, f32_rate, mhz):
         kind, masked = parts[1], parts[0] == "chain"
         if kind == "f64":
             steps = int(parts[-1][5:]) if masked else int(parts[-1][1:])
-            if not masked or steps < 256:
-                continue  # int64-key path (no probed rate); the rank path runs the float32 kernel
+            if not masked or steps < 160:
+                continue  # int64-key path (no probed rate); from 160 steps the rank path runs the float32 kernel
             kind = "f32"
         peak = peak_px_steps(nsm, u8_rate if kind == "u8" else f32_rate, mhz, kind, masked)
         out[name] = {"gpixel_steps_per_s": v["gpixel_steps_per_s"], "peak_gpixel_steps_per_s": peak / 1e9,

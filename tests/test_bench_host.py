@@ -54,7 +54,7 @@ def test_traffic_record_from_an_ncu_csv(tmp_path):
 def test_dtype_fractions_of_the_secondary_measurements():
     """Each case against its element path's peak: uint8 at 2.5 instructions
     per masked pixel-step (2 unmasked), float32 at 3 (2); float64 chains of
-    256 steps or more run the float32 kernel on ranks; reconstructions count
+    160 steps or more run the float32 kernel on ranks; reconstructions count
     the plain method's work from the oracle's changing steps."""
     sec = {"workload1_1024": {"workload": "x",
                               "chain_u8_dilate_conn8_steps1500": {"ms": 0.72, "gpixel_steps_per_s": 2000.0},
