@@ -450,18 +450,22 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
   const int64_t tpitch = (W + 3) / 4;
   const size_t tag_b = tagged ? ((2 * (size_t)tpitch * (size_t)H * 8 + 255) / 256) * 256 : 0;
   const size_t scratch_b = ctl_b + tag_b + (size_t)spitch_b * (size_t)H * (size_t)batch;
+  // A register-kernel chain of one pass (a single-tile image, or a short
+  // chain) reads the marker and writes out once: no ping-pong image, no
+  // pass epochs, no control words, so no scratch and no memset.
+  const bool one_pass = rr && mode == MODE_CHAIN && np == 1;
   void *scratch = nullptr;
-  if (fault == FAULT_ALLOC || cudaMallocFromPoolAsync(&scratch, scratch_b, ds->pool, s) != cudaSuccess)
-    return GEO_ERR_CUDA;
+  if (fault == FAULT_ALLOC) return GEO_ERR_CUDA;
+  if (!one_pass && cudaMallocFromPoolAsync(&scratch, scratch_b, ds->pool, s) != cudaSuccess) return GEO_ERR_CUDA;
   rc = GEO_OK;
-  if (cudaMemsetAsync(scratch, 0, ctl_b + tag_b, s) != cudaSuccess) rc = GEO_ERR_CUDA;
+  if (!one_pass && cudaMemsetAsync(scratch, 0, ctl_b + tag_b, s) != cudaSuccess) rc = GEO_ERR_CUDA;
 
   TileLaunch L;
   memset(&L, 0, sizeof(L));
   L.marker = make_plane(marker, pitch_b, dt, rr);
   L.mask = make_plane(mask, pitch_b, dt, rr);
   L.out = make_plane(out, pitch_b, dt, rr);
-  L.scratch = make_plane((char *)scratch + ctl_b + tag_b, spitch_b, dt, rr);
+  L.scratch = make_plane(one_pass ? nullptr : (char *)scratch + ctl_b + tag_b, spitch_b, dt, rr);
   L.marker.bstride = L.out.bstride = H * pitch_b;
   L.mask.bstride = mask ? H * pitch_b : 0;
   L.scratch.bstride = H * spitch_b;
@@ -478,8 +482,8 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
   L.steps = steps;
   L.alias = alias ? 1 : 0;
   L.ctl = (Control *)scratch;
-  L.epoch = (int *)((char *)scratch + 256);
-  L.tchg = L.epoch + ntiles;
+  L.epoch = one_pass ? nullptr : (int *)((char *)scratch + 256);
+  L.tchg = one_pass ? nullptr : L.epoch + ntiles;
   L.status = ds->status;
   L.steps_out = steps_out;
   L.fault = fault == FAULT_TIMEOUT ? 1 : 0;
@@ -491,7 +495,7 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
     L.tplane = tpitch * H;
   }
   if (rc == GEO_OK) rc = rr ? launch_rr(dt, L, op, conn, s, P) : launch_plan(dt, L, op, conn, s, P);
-  if (cudaFreeAsync(scratch, s) != cudaSuccess && rc == GEO_OK) rc = GEO_ERR_CUDA;
+  if (scratch && cudaFreeAsync(scratch, s) != cudaSuccess && rc == GEO_OK) rc = GEO_ERR_CUDA;
   return rc;
 }
 

@@ -2,10 +2,34 @@
 // element-type translation unit so the three instantiations compile in parallel).
 #pragma once
 
+#include <mutex>
+#include <set>
+#include <tuple>
+
 #include "geo_rr.cuh"
 #include "geo_tile.cuh"
 
 namespace geo {
+
+// The kernel's dynamic shared-memory limit, set once per device, kernel and
+// size (the attribute is a driver call; single-pass calls are short enough
+// for it to show).
+static inline cudaError_t set_smem_limit(void *k, int smem) {
+  static std::mutex mu;
+  static std::set<std::tuple<int, void *, int>> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (done.count(std::make_tuple(dev, k, smem))) return cudaSuccess;
+  }
+  const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> g(mu);
+    done.insert(std::make_tuple(dev, k, smem));
+  }
+  return e;
+}
 
 template <template <int> class EP>
 static void *tile_kernel_ptr(int op, int conn) {
@@ -16,7 +40,7 @@ static void *tile_kernel_ptr(int op, int conn) {
 template <template <int> class EP>
 static int launch_tile_impl(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid, size_t smem) {
   void *k = tile_kernel_ptr<EP>(op, conn);
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (set_smem_limit(k, (int)smem) != cudaSuccess)
     return GEO_ERR_CUDA;
   TileLaunch arg = L;
   void *args[] = {(void *)&arg};
@@ -27,7 +51,7 @@ static int launch_tile_impl(const TileLaunch &L, int op, int conn, cudaStream_t 
 template <template <int> class EP>
 static int occupancy_impl(int op, int conn, size_t smem, int *bps) {
   void *k = tile_kernel_ptr<EP>(op, conn);
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (set_smem_limit(k, (int)smem) != cudaSuccess)
     return GEO_ERR_CUDA;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, kThreads, smem) == cudaSuccess ? GEO_OK
                                                                                                 : GEO_ERR_CUDA;
@@ -52,7 +76,7 @@ template <template <int> class RP>
 static int launch_rr_impl(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid) {
   void *k = rr_kernel_ptr<RP>(op, conn, L.tagged != nullptr);
   const size_t smem = rr_smem_bytes<RP<DILATE>>();
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (set_smem_limit(k, (int)smem) != cudaSuccess)
     return GEO_ERR_CUDA;
   TileLaunch arg = L;
   void *args[] = {(void *)&arg};
@@ -64,7 +88,7 @@ template <template <int> class RP>
 static int occupancy_rr_impl(int op, int conn, int *bps) {
   void *k = rr_kernel_ptr<RP>(op, conn);
   const size_t smem = rr_smem_bytes<RP<DILATE>>();
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (set_smem_limit(k, (int)smem) != cudaSuccess)
     return GEO_ERR_CUDA;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k, RP<DILATE>::NW * 32, smem) == cudaSuccess
              ? GEO_OK
