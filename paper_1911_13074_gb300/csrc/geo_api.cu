@@ -22,6 +22,7 @@ constexpr int kMaxDevices = 64;
 struct DeviceState {
   bool init = false;
   int *status = nullptr;        // sticky device-side error word
+  int *status_host = nullptr;   // pinned host slot the word is read into
   cudaMemPool_t pool = nullptr;  // library-owned stream-ordered pool
   int nsm = 0;
 };
@@ -38,6 +39,7 @@ static int device_state(DeviceState **out) {
     if (cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GEO_ERR_CUDA;
     if (cudaMalloc(&d.status, sizeof(int)) != cudaSuccess) return GEO_ERR_CUDA;
     if (cudaMemset(d.status, 0, sizeof(int)) != cudaSuccess) return GEO_ERR_CUDA;
+    if (cudaMallocHost(&d.status_host, sizeof(int)) != cudaSuccess) return GEO_ERR_CUDA;
     cudaMemPoolProps props;
     memset(&props, 0, sizeof(props));
     props.allocType = cudaMemAllocationTypePinned;
@@ -433,7 +435,9 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
   const int64_t spitch_b = ((W * es + 15) / 16) * 16;
   const size_t ntiles = (size_t)P.tiles_x * (size_t)P.tiles_y * (size_t)batch;
   // [control 256 B][per-tile pass epochs][per-tile changed flags, two passes]
-  const size_t ctl_b = 256 + ((3 * ntiles * sizeof(int) + 255) / 256) * 256;
+  // [tagged reconstruction: pass ring of done counts, change counts, outcomes; abort flag]
+  const size_t ring_b = ((3 * (size_t)kRecRing + 1) * sizeof(int) + 255) / 256 * 256;
+  const size_t ctl_b = 256 + ((3 * ntiles * sizeof(int) + 255) / 256) * 256 + (mode == MODE_REC ? ring_b : 0);
   int64_t np = 0;
   if (mode == MODE_CHAIN) {
     np = rr ? rr_passes(steps, single_tile(P, batch) ? 0 : P.K) : cdiv(steps, P.K);
@@ -444,8 +448,11 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
   // over in two zeroed planes of tagged words (GEOMORPH_TAGGED=0: plain
   // planes and tile epochs); the lane's 4 columns must be whole words. From
   // 3 passes on: zeroing the planes costs about as much as one hand-over saves.
+  // Reconstruction of several tiles, one per CTA, hands over the same way
+  // and finds its fixed point without a grid barrier (rr_kernel).
   const char *tg = getenv("GEOMORPH_TAGGED");
-  const bool tagged = rr && dt == GEO_U8 && mode == MODE_CHAIN && batch == 1 && np >= kTaggedMinPasses &&
+  const bool tagged = rr && dt == GEO_U8 && batch == 1 &&
+                      ((mode == MODE_CHAIN && np >= kTaggedMinPasses) || (mode == MODE_REC && ntiles >= 2)) &&
                       ntiles <= (size_t)P.grid && P.K % 4 == 0 && P.TW % 4 == 0 && !(tg && strcmp(tg, "0") == 0);
   const int64_t tpitch = (W + 3) / 4;
   const size_t tag_b = tagged ? ((2 * (size_t)tpitch * (size_t)H * 8 + 255) / 256) * 256 : 0;
@@ -493,6 +500,13 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
     L.tagged = (unsigned long long *)((char *)scratch + ctl_b);
     L.tpitch = tpitch;
     L.tplane = tpitch * H;
+  }
+  if (mode == MODE_REC) {
+    char *ring = (char *)scratch + ctl_b - ring_b;
+    L.rec_done = (int *)ring;
+    L.rec_chg = L.rec_done + kRecRing;
+    L.rec_res = (unsigned *)(L.rec_chg + kRecRing);
+    L.rec_abort = (int *)(L.rec_res + kRecRing);
   }
   if (rc == GEO_OK) rc = rr ? launch_rr(dt, L, op, conn, s, P) : launch_plan(dt, L, op, conn, s, P);
   if (scratch && cudaFreeAsync(scratch, s) != cudaSuccess && rc == GEO_OK) rc = GEO_ERR_CUDA;
@@ -548,19 +562,27 @@ int geo_device_status(void *stream, int *status) {
   if (!status) return GEO_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GEO_ERR_CUDA;
-  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return GEO_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
   // the library's word, if this device has one (no device state is created
   // here, so a caller of the no-allocation chain allocates nothing by asking)
-  int *word = nullptr;
+  int *word = nullptr, *host = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (g_dev[dev].init) word = g_dev[dev].status;
+    if (g_dev[dev].init) {
+      word = g_dev[dev].status;
+      host = g_dev[dev].status_host;
+    }
   }
-  int v = 0;
+  // read and clear in the stream's order after its work, one synchronisation
+  // (the pinned slot is shared by the device's readers: one at a time)
+  static std::mutex read_mu;
+  std::lock_guard<std::mutex> rl(read_mu);
   if (word) {
-    if (cudaMemcpy(&v, word, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return GEO_ERR_CUDA;
-    if (cudaMemset(word, 0, sizeof(int)) != cudaSuccess) return GEO_ERR_CUDA;
+    if (cudaMemcpyAsync(host, word, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return GEO_ERR_CUDA;
+    if (cudaMemsetAsync(word, 0, sizeof(int), s) != cudaSuccess) return GEO_ERR_CUDA;
   }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return GEO_ERR_CUDA;
+  const int v = word ? *host : 0;
   // and the no-allocation chain's word
   int w = 0;
   if (noalloc_take_status(dev, &w) != GEO_OK) return GEO_ERR_CUDA;

@@ -103,7 +103,21 @@ struct TileLaunch {
   // nullptr: off
   unsigned long long *tagged;
   int64_t tpitch, tplane;  // words per row / per plane of `tagged`
+  // register kernel, uint8 reconstruction with tagged planes (one tile per
+  // CTA): per-pass counters in a ring of kRecRing slots, zeroed with the
+  // control words: tiles done with the pass, tiles whose interior changed in
+  // the pass's last step, the pass's outcome ((pass + 1) << 2 | 1 changed,
+  // | 2 unchanged), and a flag set by a tile whose wait expired
+  int *rec_done, *rec_chg;
+  unsigned *rec_res;
+  int *rec_abort;
 };
+
+// Ring of per-pass reconstruction counters: a tile is at most one pass ahead
+// of each neighbour, so no two tiles are more than (tiles - 1) passes apart
+// (at most 2 CTAs per SM, 304 tiles on 152 SMs), and a slot is reused only
+// after every tile has finished the pass that used it before.
+constexpr int kRecRing = 512;
 
 // Passes of a chain of `steps` with halo K; K = 0 for a single-tile plan of
 // the register kernel. When one tile covers the image (one image, one tile),

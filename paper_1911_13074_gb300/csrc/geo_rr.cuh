@@ -728,8 +728,22 @@ struct RR {
   // Load the lane's region rows from the tagged plane T, waiting (bounded)
   // until every word inside the image carries `tag`. Rows and columns
   // outside the image take the identity. False if the wait expired.
+  struct NeverStop {
+    __device__ bool operator()() const { return false; }
+  };
   __device__ static bool load_tagged(const unsigned long long *T, int64_t tpitch, int64_t H, int64_t W, int64_t gy0,
                                      int64_t gx, unsigned tag, unsigned long long limit_ns, Wd (&w)[RW][CW]) {
+    NeverStop never;
+    return load_tagged_or_stop(T, tpitch, H, W, gy0, gx, tag, limit_ns, w, never) == 1;
+  }
+
+  // The same, but while waiting the lane also asks `stop` now and then; when
+  // it answers true the lane gives up and leaves w as it was. 1 = loaded,
+  // 0 = the wait expired, 2 = stopped.
+  template <class Stop>
+  __device__ static int load_tagged_or_stop(const unsigned long long *T, int64_t tpitch, int64_t H, int64_t W,
+                                            int64_t gy0, int64_t gx, unsigned tag, unsigned long long limit_ns,
+                                            Wd (&w)[RW][CW], const Stop &stop) {
     static_assert(kTagged, "tagged planes hold uint8 pixels");
     constexpr int NR = B * RW;
     const bool cols = gx >= 0 && gx < W;
@@ -755,9 +769,12 @@ struct RR {
         if (((in >> i) & 1u) && (unsigned)(raw[i] >> 32) != tag) miss |= 1u << i;
       if (!miss) break;
       if (n == 0) t0 = globaltimer_ns();
-      if ((++n & 15u) == 0 && globaltimer_ns() - t0 > limit_ns) {
-        ok = false;
-        break;
+      if ((++n & 15u) == 0) {
+        if (stop()) return 2;
+        if (globaltimer_ns() - t0 > limit_ns) {
+          ok = false;
+          break;
+        }
       }
 #pragma unroll
       for (int i = 0; i < NR; ++i)
@@ -776,7 +793,7 @@ struct RR {
         w[r][c] = P::make(lo[c], hi[c]);
       }
     }
-    return ok;
+    return ok ? 1 : 0;
   }
 };
 
@@ -821,6 +838,56 @@ __device__ __forceinline__ int any_neighbour_changed(const int *flags, int ty, i
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// reconstruction with tagged planes (uint8, one tile per CTA)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned *p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+// The outcome of the passes from `chk` on, before pass `upto`: the first
+// pass whose last step changed no pixel anywhere (the image is then a fixed
+// point), -1 while none is known, -2 once a tile has given up. chk advances
+// over the passes known to have changed something.
+__device__ __forceinline__ int rec_poll(const TileLaunch &L, int &chk, int upto) {
+  if (ld_acquire_u32(reinterpret_cast<const unsigned *>(L.rec_abort))) return -2;
+  while (chk < upto) {
+    const unsigned r = ld_acquire_u32(L.rec_res + (chk % kRecRing));
+    if ((r >> 2) != (unsigned)(chk + 1)) return -1;  // not decided yet
+    if ((r & 3u) == 2u) return chk;
+    ++chk;
+  }
+  return -1;
+}
+
+// Stop test of a tile waiting for its neighbours' words: the fixed point is
+// known, or some tile gave up.
+struct RecStop {
+  const TileLaunch *L;
+  int chk;
+  __device__ bool operator()() const {
+    int c = chk;
+    return rec_poll(*L, c, 0x7fffffff) != -1;
+  }
+};
+
+// Observer of a pass's last step: whether any pixel of the tile's interior
+// (and inside the image) changed. colmask: the lane's interior columns (bit
+// c); rowmask[r]: the interior rows among the two u16 lanes of word row r.
+template <class P>
+struct InteriorChange {
+  uint32_t colmask;
+  uint32_t rowmask[P::RW];
+  bool changed;
+  template <class Wd>
+  __device__ __forceinline__ void operator()(int r, int c, Wd old, Wd nv) {
+    if ((colmask >> c) & 1u) changed |= ((old ^ nv) & rowmask[r]) != 0u;
+  }
+};
+
 template <class P>
 constexpr size_t rr_smem_bytes() {
   return sizeof(typename P::Wd) * 2 * (P::NW + 2) * 2 * 32 * P::CW;
@@ -850,8 +917,9 @@ __global__ void __launch_bounds__(P::NW * 32, P::NW <= 8 ? 2 : 1) rr_kernel(cons
   const bool rec = (L.mode == MODE_REC);
   const bool virt = (L.mask.ptr == nullptr);
   const bool mask_resident = (ntiles <= (int)gridDim.x);
-  // tagged hand-over between chain passes (one tile per CTA, uint8)
-  const bool tagged = TAG && !rec && L.tagged != nullptr && mask_resident;
+  // tagged hand-over between passes (one tile per CTA, uint8): chains, and
+  // reconstruction in its own loop below
+  const bool tagged = TAG && L.tagged != nullptr && mask_resident;
 
   __shared__ __align__(8) uint64_t xbar;  // split-phase step barrier of the whole CTA
   if (threadIdx.x == 0) mbar_init(&xbar, NW * 32);
@@ -866,6 +934,158 @@ __global__ void __launch_bounds__(P::NW * 32, P::NW <= 8 ? 2 : 1) rr_kernel(cons
   Wd w[RW][CW], m[RW][CW];
   int64_t steps_left = L.steps, steps_done = 0;
   int parity = 0;  // parity of the steps done by this CTA: exchange buffer and barrier phase
+
+  if constexpr (TAG) {
+    if (rec && tagged) {
+      // Reconstruction with the tagged hand-over: no grid barrier. After each
+      // pass a tile reports whether the pass's last step changed a pixel of
+      // its interior (one counter pair per pass, in a ring); the last tile to
+      // report a pass publishes its outcome. A step that changes nothing
+      // anywhere means the image is a fixed point (the step is a function of
+      // the image), so the first pass whose last step changed nothing is the
+      // last one needed. Tiles go on to the next passes meanwhile (at most one
+      // pass ahead of any neighbour, as in a chain) and stop at the start of
+      // a pass, or while waiting for a neighbour's words, once they know that
+      // outcome; the registers then hold a later pass's interior, which is the
+      // same fixed point, and go to out.
+      __shared__ int rs_stop, rs_chk;
+      const int t = blockIdx.x;
+      if (t < ntiles) {
+        const int ty = t / L.tiles_x, tx = t - ty * L.tiles_x;
+        const int64_t ty0 = (int64_t)ty * TH, tx0 = (int64_t)tx * TW;
+        const int64_t gy0 = ty0 - K + warp * PH;
+        const int64_t gx = tx0 - K + lane * CW;
+        R::load_words(L.mask, L.H, L.W, gy0, gx, false, virt, m);
+        R::load_words(L.marker, L.H, L.W, gy0, gx, L.marker.ptr == L.out.ptr, false, w);
+        InteriorChange<P> ic;
+        ic.colmask = 0;
+        ic.changed = false;
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+          const int X = lane * CW + c;
+          if (X >= K && X < K + TW && tx0 + (X - K) < L.W) ic.colmask |= 1u << c;
+        }
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+          uint32_t rm = 0;
+#pragma unroll
+          for (int b = 0; b < R::B; ++b) {
+            const int Y = warp * PH + b * RW + r;
+            if (Y >= K && Y < K + TH && ty0 + (Y - K) < L.H) rm |= 0xffffu << (16 * b);
+          }
+          ic.rowmask[r] = rm;
+        }
+        int chk = 0, stop_pass = -1;
+        bool aborted = false;
+        int64_t left = L.steps, done = 0;
+        for (int q = 0;; ++q) {
+          if (q > 0) {
+            if (threadIdx.x == 0) {
+              rs_stop = rec_poll(L, chk, q);
+              rs_chk = chk;
+            }
+            __syncthreads();
+            int sp = rs_stop;
+            if (sp == -1) {
+              // this pass's region: the previous pass's words of this tile and
+              // its neighbours, unless the fixed point becomes known meanwhile
+              RecStop stop{&L, rs_chk};
+              const unsigned want = L.fault ? (unsigned)q + (1u << 28) : (unsigned)q;
+              const int lr = R::load_tagged_or_stop(L.tagged + (size_t)((q - 1) & 1) * L.tplane, L.tpitch, L.H, L.W,
+                                                    gy0, gx, want, L.wait_ns, w, stop);
+              const int failed = __syncthreads_or(lr == 0);
+              const int stopped = __syncthreads_or(lr == 2);
+              if (failed) {
+                if (threadIdx.x == 0) {
+                  record_status(L.status, GEO_ERR_TIMEOUT);
+                  atomicExch(L.rec_abort, 1);
+                }
+                aborted = true;
+                break;
+              }
+              if (stopped) {
+                if (threadIdx.x == 0) rs_stop = rec_poll(L, chk, 0x7fffffff);
+                __syncthreads();
+                sp = rs_stop;
+              }
+            }
+            if (sp >= 0) {
+              stop_pass = sp;
+              break;
+            }
+            if (sp == -2) {
+              aborted = true;
+              break;
+            }
+          }
+          const int S = (int)(left < K ? left : K);
+          bool ok = true;
+          ic.changed = false;
+          for (int j = 0; j < S; ++j) {
+            if (j == S - 1) ok &= R::template step<CONN>(w, m, &xbuf[parity][0][0][0], &xbar, parity, lane, warp, ic);
+            else ok &= R::template step<CONN>(w, m, &xbuf[parity][0][0][0], &xbar, parity, lane, warp);
+            parity ^= 1;
+          }
+          const int tile_changed = __syncthreads_or(ic.changed ? 1 : 0);
+          if (__syncthreads_or(ok ? 0 : 1)) {
+            if (threadIdx.x == 0) {
+              record_status(L.status, GEO_ERR_TIMEOUT);
+              atomicExch(L.rec_abort, 1);
+            }
+            aborted = true;
+            break;
+          }
+          R::store_tagged(w, L.tagged + (size_t)(q & 1) * L.tplane, L.tpitch, L.H, L.W, ty0, tx0, K, TH, TW,
+                          (unsigned)(q + 1), lane, warp);
+          left -= S;
+          done += S;
+          if (threadIdx.x == 0) {
+            const int slot = q % kRecRing;
+            if (tile_changed) atomicAdd(L.rec_chg + slot, 1);
+            const unsigned old = atom_add_acq_rel_u32(reinterpret_cast<unsigned *>(L.rec_done + slot), 1u);
+            if (old == (unsigned)(ntiles - 1)) {
+              // the last tile of pass q: every other tile's change count came
+              // before its release on done, which this acquire has seen
+              const unsigned c = ld_acquire_u32(reinterpret_cast<const unsigned *>(L.rec_chg + slot));
+              L.rec_chg[slot] = 0;
+              L.rec_done[slot] = 0;
+              st_release_u32(L.rec_res + slot, ((unsigned)(q + 1) << 2) | (c ? 1u : 2u));
+            }
+          }
+          if (left <= 0) {
+            // the step cap: this pass's outcome decides between a fixed point
+            // and GEO_ERR_NOT_CONVERGED (every tile reaches the cap together)
+            if (threadIdx.x == 0) {
+              int sp = -1;
+              const unsigned long long t0 = globaltimer_ns();
+              unsigned spins = 0;
+              while ((sp = rec_poll(L, chk, q + 1)) == -1 && chk <= q) {
+                if ((++spins & 255u) == 0 && globaltimer_ns() - t0 > L.wait_ns) {
+                  record_status(L.status, GEO_ERR_TIMEOUT);
+                  atomicExch(L.rec_abort, 1);
+                  sp = -2;
+                  break;
+                }
+              }
+              rs_stop = sp;
+            }
+            __syncthreads();
+            const int sp = rs_stop;
+            if (sp >= 0) stop_pass = sp;
+            else if (sp == -2) aborted = true;
+            else if (t == 0 && threadIdx.x == 0) record_status(L.status, GEO_ERR_NOT_CONVERGED);
+            break;
+          }
+        }
+        if (!aborted) R::store(w, L.out, L.out, false, L.H, L.W, ty0, tx0, K, TH, TW, lane, warp);
+        if (L.steps_out && t == 0 && threadIdx.x == 0) {
+          const int64_t applied = (int64_t)(stop_pass + 1) * K;
+          *L.steps_out = stop_pass >= 0 ? (applied < L.steps ? applied : L.steps) : done;
+        }
+      }
+      return;
+    }
+  }
   for (int pass = 0;; ++pass) {
     int S;
     if (!rec) {
