@@ -178,6 +178,36 @@ def test_reconstruct_not_converged_status():
     assert e.value.code == -6
 
 
+def test_tagged_reconstruction_cap_and_step_count(monkeypatch):
+    """uint8 reconstruction of several tiles (one per CTA) runs on tagged
+    words with a per-pass vote instead of a grid barrier: the fixed point
+    equals the oracle's, the steps it reports cover the oracle's changing
+    steps plus the step that changes nothing, and capped below its length it
+    records GEO_ERR_NOT_CONVERGED with out holding exactly the chain of the
+    capped number of steps (each pass runs min(K, steps left))."""
+    monkeypatch.delenv("GEOMORPH_TAGGED", raising=False)
+    monkeypatch.delenv("GEOMORPH_KERNEL", raising=False)
+    m = gm()
+    w = synth.workload0(300, 420)
+    f, msk = w["marker"], w["mask"]
+    K, TH, TW = m.plan_info(torch.uint8, "dilate_rec", 8, 300, 420, 0)
+    assert -(-300 // TH) * -(-420 // TW) >= 2  # several tiles
+    out, steps = m.reconstruct(dev(f), dev(msk), return_steps=True)
+    ref, n = oracle.reconstruct(f, msk)
+    assert_same(host(out), ref, "tagged reconstruction")
+    assert int(steps.item()) >= n + 1
+    for cap in (37, 2 * K + 3):
+        o = m.reconstruct(dev(f), dev(msk), max_steps=cap, check=False)
+        assert m.device_status() == -6
+        assert_same(host(o), oracle.chain(f, msk, cap), f"capped at {cap}")
+    # erosion, in place, 4-connected
+    e = np.minimum(msk.astype(np.int64) + 40, 255).astype(np.uint8)
+    t = dev(e)
+    m.reconstruct(t, dev(msk), conn=4, op="erode", out=t)
+    assert_same(host(t), oracle.reconstruct(e, msk, conn=4, op="erode")[0], "tagged erosion, in place")
+    assert m.device_status() == 0
+
+
 def test_full_size_1024_u8_chain(kernel):
     """1024x1024 u8 (workload 1), 100-step chains of both operations, whole image."""
     w = synth.workload1_u8()
