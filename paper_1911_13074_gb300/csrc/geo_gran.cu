@@ -336,6 +336,181 @@ int open_close(int first, geo_dtype dt, const void *f, void *out, int64_t H, int
   return run_program(dt, f, out, H, W, pitch, ops, steps, 2, (cudaStream_t)stream);
 }
 
+// ---------------------------------------------------------------------------
+// granulometry in one launch per size: gamma_k = delta_k(eps_k(f)) (Eq. 16)
+// with eps_k = eps_1(eps_{k-1}) kept from size to size (Eq. 17's G_k needs
+// only the sum of gamma_k, so gamma_k itself is never stored)
+// ---------------------------------------------------------------------------
+
+// One tile per CTA and pass, tiles independent within the launch: the region
+// of eps_{k-1} with a halo of at least k + 1 (gran_halo), one erosion step (its interior is
+// eps_k, stored for size k + 1), then k dilation steps on the same
+// registers; the interior of the result is gamma_k, summed into partial[t].
+// Between the two operations the rows beyond the region take the dilation's
+// identity and the region's cells outside the image are clamped to it.
+template <template <int> class RP>
+__global__ void __launch_bounds__(RP<DILATE>::NW * 32, 1) gran_kernel(const TileLaunch L, int k,
+                                                                       double *__restrict__ partial) {
+  using PD = RP<DILATE>;
+  using PE = RP<ERODE>;
+  using RE = RR<PE>;
+  using RD = RR<PD>;
+  using Wd = typename PD::Wd;
+  constexpr int CW = PD::CW, RW = PD::RW, NW = PD::NW, RWID = 32 * CW, PH = RW * PD::BANDS;
+  extern __shared__ __align__(16) char rr_dyn[];
+  Wd(*xbuf)[NW + 2][2][RWID] = reinterpret_cast<Wd(*)[NW + 2][2][RWID]>(rr_dyn);
+  __shared__ __align__(8) uint64_t xbar;
+  __shared__ double red[NW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) mbar_init(&xbar, NW * 32);
+  const int K = L.K, TH = L.TH, TW = L.TW;
+  const int ntiles = L.tiles_x * L.tiles_y;
+  int parity = 0;
+  bool ok = true;
+  Wd w[RW][CW], m[RW][CW];
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int ty = t / L.tiles_x, tx = t - ty * L.tiles_x;
+    const int64_t ty0 = (int64_t)ty * TH, tx0 = (int64_t)tx * TW;
+    const int64_t gy0 = ty0 - K + warp * PH, gx = tx0 - K + lane * CW;
+    __syncthreads();  // the previous tile's steps are done with the exchange rows
+    for (int i = threadIdx.x; i < 2 * 2 * RWID; i += NW * 32) {
+      const int par = i / (2 * RWID), rest = i % (2 * RWID);
+      (&xbuf[par][0][0][0])[rest] = PE::identw();
+      (&xbuf[par][NW + 1][0][0])[rest] = PE::identw();
+    }
+    __syncthreads();
+    RE::load_words(L.marker, L.H, L.W, gy0, gx, true, false, w);
+    RE::load_words(L.marker, L.H, L.W, gy0, gx, false, true, m);  // the erosion's virtual mask
+    ok &= RE::template step<8>(w, m, &xbuf[parity][0][0][0], &xbar, parity, lane, warp);
+    parity ^= 1;
+    RE::store(w, L.out, L.out, false, L.H, L.W, ty0, tx0, K, TH, TW, lane, warp);  // eps_k
+    __syncthreads();  // every warp past the erosion step's exchange
+    for (int i = threadIdx.x; i < 2 * 2 * RWID; i += NW * 32) {
+      const int par = i / (2 * RWID), rest = i % (2 * RWID);
+      (&xbuf[par][0][0][0])[rest] = PD::identw();
+      (&xbuf[par][NW + 1][0][0])[rest] = PD::identw();
+    }
+    __syncthreads();
+    RD::load_words(L.marker, L.H, L.W, gy0, gx, false, true, m);  // the dilation's virtual mask
+#pragma unroll
+    for (int r = 0; r < RW; ++r)
+#pragma unroll
+      for (int c = 0; c < CW; ++c) w[r][c] = PD::clamp(w[r][c], m[r][c]);
+    for (int j = 0; j < k; ++j) {
+      ok &= RD::template step<8>(w, m, &xbuf[parity][0][0][0], &xbar, parity, lane, warp);
+      parity ^= 1;
+    }
+    // sum of gamma_k over the tile's interior cells inside the image
+    double acc = 0.0;
+#pragma unroll
+    for (int b = 0; b < PD::BANDS; ++b)
+#pragma unroll
+      for (int r = 0; r < RW; ++r) {
+        const int Y = warp * PH + b * RW + r;
+        if (Y < K || Y >= K + TH || ty0 + (Y - K) >= L.H) continue;
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+          const int X = lane * CW + c;
+          if (X < K || X >= K + TW || tx0 + (X - K) >= L.W) continue;
+          acc += (double)PD::from_px(PD::get(w[r][c], b));
+        }
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int i = 0; i < NW; ++i) sum += red[i];
+      partial[t] = sum;
+    }
+  }
+  if (!ok && threadIdx.x == 0) record_status(L.status, GEO_ERR_TIMEOUT);
+}
+
+// G[1 + b] = sum of partial[b * stride .. b * stride + stride) in a fixed tree
+// order (one block per size; unused entries are zero)
+__global__ void __launch_bounds__(kSumBlocks) gran_final(const double *__restrict__ partial, int stride, double *G) {
+  __shared__ double red[kSumBlocks];
+  const double *p = partial + (size_t)blockIdx.x * stride;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < stride; i += kSumBlocks) acc += p[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kSumBlocks / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) G[1 + blockIdx.x] = red[0];
+}
+
+// The largest size the fused launch takes for an element type: the halo
+// within a third of the register region's shorter side (as the planner's
+// K), so that the interior keeps at least a third of it; and the per-tile
+// sums' stride (the tiles of the largest size, which has the most).
+// The halo is k + 1 rounded up to whole lanes (CW columns), as every pass
+// of the register kernel: a lane's columns then lie wholly in the interior
+// or wholly in the halo.
+template <template <int> class RP>
+int gran_halo(int64_t k) {
+  constexpr int CW = RP<DILATE>::CW;
+  return (int)((k + 1 + CW - 1) / CW * CW);
+}
+template <template <int> class RP>
+int gran_fused_max() {
+  using PD = RP<DILATE>;
+  constexpr int RWID = 32 * PD::CW, RHGT = PD::NW * PD::RW * PD::BANDS;
+  return (RWID < RHGT ? RWID : RHGT) / 3 / PD::CW * PD::CW - 1;
+}
+template <template <int> class RP>
+int gran_fused_tiles(int64_t H, int64_t W, int64_t smax) {
+  using PD = RP<DILATE>;
+  constexpr int RWID = 32 * PD::CW, RHGT = PD::NW * PD::RW * PD::BANDS;
+  const int K = gran_halo<RP>(smax);
+  return (int)(((H + (RHGT - 2 * K) - 1) / (RHGT - 2 * K)) * ((W + (RWID - 2 * K) - 1) / (RWID - 2 * K)));
+}
+
+template <template <int> class RP>
+int gran_fused(const void *f, int64_t H, int64_t W, int64_t pitch, int64_t smax, double *G, cudaStream_t s,
+               char *eps_a, char *eps_b, double *partial, int stride, int *status) {
+  using PD = RP<DILATE>;
+  constexpr int RWID = 32 * PD::CW, RHGT = PD::NW * PD::RW * PD::BANDS;
+  void *kern = (void *)gran_kernel<RP>;
+  const size_t smem = rr_smem_bytes<PD>();
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return GEO_ERR_CUDA;
+  const int es = (int)sizeof(typename PD::G);
+  const size_t va = (size_t)PD::CW * es;
+  const void *src = f;
+  for (int64_t k = 1; k <= smax; ++k) {
+    char *dst = (k & 1) ? eps_a : eps_b;
+    TileLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.K = gran_halo<RP>(k);
+    L.TH = RHGT - 2 * L.K;
+    L.TW = RWID - 2 * L.K;
+    L.tiles_x = (int)((W + L.TW - 1) / L.TW);
+    L.tiles_y = (int)((H + L.TH - 1) / L.TH);
+    L.marker = prog_plane(src, pitch * es, va);
+    L.out = prog_plane(dst, pitch * es, va);
+    L.mask = prog_plane(nullptr, 0, 1);
+    L.H = H;
+    L.W = W;
+    L.status = status;
+    L.wait_ns = kWaitLimitNs;
+    const int ntiles = L.tiles_x * L.tiles_y;
+    if (ntiles > stride) return GEO_ERR_ARG;
+    TileLaunch a = L;
+    int kk = (int)k;
+    double *pk = partial + (size_t)(k - 1) * stride;
+    void *args[] = {(void *)&a, (void *)&kk, (void *)&pk};
+    if (cudaLaunchKernel(kern, dim3(ntiles), dim3(PD::NW * 32), args, smem, s) != cudaSuccess) return GEO_ERR_CUDA;
+    src = dst;
+  }
+  gran_final<<<(unsigned)smax, kSumBlocks, 0, s>>>(partial, stride, G);
+  return cudaGetLastError() == cudaSuccess ? GEO_OK : GEO_ERR_CUDA;
+}
+
 }  // namespace
 }  // namespace geo
 
@@ -410,16 +585,38 @@ int geo_granulometry(geo_dtype dtype, const void *f, int64_t height, int64_t wid
   }
   if (!f) return GEO_ERR_ARG;
   const int es = elem_bytes(dtype);
-  // scratch: [partial sums][eps_s(f)][gamma_s(f)], images with f's pitch
+  // scratch: [partial sums][eps_s(f)][gamma_s(f) or eps_s(f)], images with
+  // f's pitch; the fused form's per-tile sums of every size after them
   const size_t part_b = kSumBlocks * sizeof(double);
   const size_t img_b = (((size_t)((H - 1) * pitch + W) * es) + 255) / 256 * 256;
+  // Sizes up to gran_fused_max run one launch each (erosion step, dilation
+  // steps and the interior sums of every tile together); larger ones go
+  // through the window calls, one erosion step, one window and one sum each.
+  const int fmax = dtype == GEO_U8 ? gran_fused_max<SU8>() : dtype == GEO_F32 ? gran_fused_max<SF32>()
+                                                                              : gran_fused_max<SF64>();
+  const bool fused = smax >= 1 && smax <= fmax;
+  const int stride = !fused ? 0
+                     : dtype == GEO_U8  ? gran_fused_tiles<SU8>(H, W, smax)
+                     : dtype == GEO_F32 ? gran_fused_tiles<SF32>(H, W, smax)
+                                        : gran_fused_tiles<SF64>(H, W, smax);
   void *scratch = nullptr;
-  int rc = pool_alloc(&scratch, part_b + 2 * img_b, s);
+  int rc = pool_alloc(&scratch, part_b + 2 * img_b + (size_t)smax * stride * sizeof(double), s);
   if (rc != GEO_OK) return rc;
   double *partial = (double *)scratch;
   char *ero = (char *)scratch + part_b, *gam = ero + img_b;
+  double *tile_sums = (double *)(gam + img_b);
   rc = image_sum(dtype, f, H, W, pitch, partial, G, s);
-  for (int64_t k = 1; k <= smax && rc == GEO_OK; ++k) {
+  if (fused && rc == GEO_OK) {
+    int *status = nullptr;
+    rc = device_status_word(&status);
+    if (rc == GEO_OK && cudaMemsetAsync(tile_sums, 0, (size_t)smax * stride * sizeof(double), s) != cudaSuccess)
+      rc = GEO_ERR_CUDA;
+    if (rc == GEO_OK)
+      rc = dtype == GEO_U8 ? gran_fused<SU8>(f, H, W, pitch, smax, G, s, ero, gam, tile_sums, stride, status)
+           : dtype == GEO_F32 ? gran_fused<SF32>(f, H, W, pitch, smax, G, s, ero, gam, tile_sums, stride, status)
+                              : gran_fused<SF64>(f, H, W, pitch, smax, G, s, ero, gam, tile_sums, stride, status);
+  }
+  for (int64_t k = 1; !fused && k <= smax && rc == GEO_OK; ++k) {
     rc = window(ERODE, dtype, k == 1 ? f : ero, ero, H, W, pitch, 1, stream);
     if (rc == GEO_OK) rc = window(DILATE, dtype, ero, gam, H, W, pitch, k, stream);
     if (rc == GEO_OK) rc = image_sum(dtype, gam, H, W, pitch, partial, G + k, s);

@@ -74,6 +74,28 @@ def test_granulometry_matches_oracle(H, W, kind):
         assert np.abs(G - Go).max() <= tol and np.abs(PS - PSo).max() <= 2 * tol
 
 
+@pytest.mark.parametrize("kind,smax", [("u8", 39), ("u8", 41), ("f64", 19), ("f64", 21), ("f32", 9)])
+def test_granulometry_fused_sizes_and_fallback(kind, smax):
+    """The granulometry runs one launch per size (erosion step, dilation
+    steps and the per-tile sums together) while the halo (smax + 1, rounded
+    up to whole lanes) fits a third of the register region's side (sizes up
+    to 39 for uint8 and float32, 19 for float64), and the window calls
+    beyond; both equal the oracle, on an image of many tiles with ragged
+    edges."""
+    m = gm()
+    f = img(130, 150, kind)
+    G, PS = m.granulometry(torch.from_numpy(f).cuda(), smax)
+    Go, PSo = oracle.granulometry(f, smax)
+    G, PS = host(G), host(PS)
+    if kind == "u8":
+        np.testing.assert_array_equal(G, Go)
+        np.testing.assert_array_equal(PS, PSo)
+    else:
+        tol = 1e-12 * np.abs(f.astype(np.float64)).sum()
+        assert np.abs(G - Go).max() <= tol and np.abs(PS - PSo).max() <= 2 * tol
+    assert m.device_status() == 0
+
+
 def test_in_place_and_pitched():
     m = gm()
     f = synth.workload0(150, 170)["mask"]
