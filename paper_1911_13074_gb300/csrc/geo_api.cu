@@ -435,8 +435,8 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
   const int64_t spitch_b = ((W * es + 15) / 16) * 16;
   const size_t ntiles = (size_t)P.tiles_x * (size_t)P.tiles_y * (size_t)batch;
   // [control 256 B][per-tile pass epochs][per-tile changed flags, two passes]
-  // [tagged reconstruction: pass ring of done counts, change counts, outcomes; abort flag]
-  const size_t ring_b = ((3 * (size_t)kRecRing + 1) * sizeof(int) + 255) / 256 * 256;
+  // [tagged reconstruction: pass ring of votes and outcomes; abort flag]
+  const size_t ring_b = ((2 * (size_t)kRecRing + 1) * sizeof(int) + 255) / 256 * 256;
   const size_t ctl_b = 256 + ((3 * ntiles * sizeof(int) + 255) / 256) * 256 + (mode == MODE_REC ? ring_b : 0);
   int64_t np = 0;
   if (mode == MODE_CHAIN) {
@@ -504,8 +504,7 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
   if (mode == MODE_REC) {
     char *ring = (char *)scratch + ctl_b - ring_b;
     L.rec_done = (int *)ring;
-    L.rec_chg = L.rec_done + kRecRing;
-    L.rec_res = (unsigned *)(L.rec_chg + kRecRing);
+    L.rec_res = (unsigned *)(L.rec_done + kRecRing);
     L.rec_abort = (int *)(L.rec_res + kRecRing);
   }
   if (rc == GEO_OK) rc = rr ? launch_rr(dt, L, op, conn, s, P) : launch_plan(dt, L, op, conn, s, P);

@@ -104,11 +104,12 @@ struct TileLaunch {
   unsigned long long *tagged;
   int64_t tpitch, tplane;  // words per row / per plane of `tagged`
   // register kernel, uint8 reconstruction with tagged planes (one tile per
-  // CTA): per-pass counters in a ring of kRecRing slots, zeroed with the
-  // control words: tiles done with the pass, tiles whose interior changed in
-  // the pass's last step, the pass's outcome ((pass + 1) << 2 | 1 changed,
-  // | 2 unchanged), and a flag set by a tile whose wait expired
-  int *rec_done, *rec_chg;
+  // CTA): per-pass words in a ring of kRecRing slots, zeroed with the control
+  // words: the votes (tiles done with the pass in the low 16 bits, tiles
+  // whose interior changed in the pass's last step in the high 16), the
+  // pass's outcome ((pass + 1) << 2 | 1 changed, | 2 unchanged), and a flag
+  // set by a tile whose wait expired
+  int *rec_done;
   unsigned *rec_res;
   int *rec_abort;
 };

@@ -338,6 +338,11 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
   asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p));
   return v;
 }
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -939,7 +944,7 @@ __global__ void __launch_bounds__(P::NW * 32, P::NW <= 8 ? 2 : 1) rr_kernel(cons
     if (rec && tagged) {
       // Reconstruction with the tagged hand-over: no grid barrier. After each
       // pass a tile reports whether the pass's last step changed a pixel of
-      // its interior (one counter pair per pass, in a ring); the last tile to
+      // its interior (one vote word per pass, in a ring); the last tile to
       // report a pass publishes its outcome. A step that changes nothing
       // anywhere means the image is a fixed point (the step is a function of
       // the image), so the first pass whose last step changed nothing is the
@@ -978,37 +983,63 @@ __global__ void __launch_bounds__(P::NW * 32, P::NW <= 8 ? 2 : 1) rr_kernel(cons
         int chk = 0, stop_pass = -1;
         bool aborted = false;
         int64_t left = L.steps, done = 0;
+        // thread 0's vote on the previous pass: the pass's word before its
+        // own add (tiles done in the low 16 bits, tiles changed in the high
+        // ones), read only after the next pass's loads, so that the atomic's
+        // round trip overlaps them; the last tile of a pass publishes its
+        // outcome then
+        unsigned vote_old = 0, vote_mine = 0;
+        int vote_pass = -1;
+        auto settle_vote = [&]() {
+          if (vote_pass >= 0 && (vote_old & 0xffffu) == (unsigned)(ntiles - 1)) {
+            const unsigned slot = (unsigned)(vote_pass % kRecRing);
+            const bool changed = (vote_old >> 16) + vote_mine > 0u;
+            L.rec_done[slot] = 0;  // free for pass vote_pass + kRecRing
+            st_release_u32(L.rec_res + slot, ((unsigned)(vote_pass + 1) << 2) | (changed ? 1u : 2u));
+          }
+          vote_pass = -1;
+        };
         for (int q = 0;; ++q) {
           if (q > 0) {
+            // the outcome of pass chk and the abort flag, read by thread 0
+            // now and looked at after this pass's loads
+            unsigned pre_res = 0, pre_abort = 0;
             if (threadIdx.x == 0) {
-              rs_stop = rec_poll(L, chk, q);
+              pre_res = ld_relaxed_u32(L.rec_res + (chk % kRecRing));
+              pre_abort = ld_relaxed_u32(reinterpret_cast<const unsigned *>(L.rec_abort));
               rs_chk = chk;
             }
             __syncthreads();
-            int sp = rs_stop;
-            if (sp == -1) {
-              // this pass's region: the previous pass's words of this tile and
-              // its neighbours, unless the fixed point becomes known meanwhile
-              RecStop stop{&L, rs_chk};
-              const unsigned want = L.fault ? (unsigned)q + (1u << 28) : (unsigned)q;
-              const int lr = R::load_tagged_or_stop(L.tagged + (size_t)((q - 1) & 1) * L.tplane, L.tpitch, L.H, L.W,
-                                                    gy0, gx, want, L.wait_ns, w, stop);
-              const int failed = __syncthreads_or(lr == 0);
-              const int stopped = __syncthreads_or(lr == 2);
-              if (failed) {
-                if (threadIdx.x == 0) {
-                  record_status(L.status, GEO_ERR_TIMEOUT);
-                  atomicExch(L.rec_abort, 1);
-                }
-                aborted = true;
-                break;
+            // this pass's region: the previous pass's words of this tile and
+            // its neighbours, unless the fixed point becomes known meanwhile
+            RecStop stop{&L, rs_chk};
+            const unsigned want = L.fault ? (unsigned)q + (1u << 28) : (unsigned)q;
+            const int lr = R::load_tagged_or_stop(L.tagged + (size_t)((q - 1) & 1) * L.tplane, L.tpitch, L.H, L.W,
+                                                  gy0, gx, want, L.wait_ns, w, stop);
+            const int failed = __syncthreads_or(lr == 0);
+            const int stopped = __syncthreads_or(lr == 2);
+            if (threadIdx.x == 0) {
+              settle_vote();
+              int sp = -1;
+              if (pre_abort) {
+                sp = -2;
+              } else if ((pre_res >> 2) == (unsigned)(chk + 1)) {
+                if ((pre_res & 3u) == 2u) sp = chk;
+                else ++chk;
               }
-              if (stopped) {
-                if (threadIdx.x == 0) rs_stop = rec_poll(L, chk, 0x7fffffff);
-                __syncthreads();
-                sp = rs_stop;
-              }
+              if (stopped && sp == -1) sp = rec_poll(L, chk, 0x7fffffff);  // a lane saw the outcome
+              rs_stop = sp;
             }
+            __syncthreads();
+            if (failed) {
+              if (threadIdx.x == 0) {
+                record_status(L.status, GEO_ERR_TIMEOUT);
+                atomicExch(L.rec_abort, 1);
+              }
+              aborted = true;
+              break;
+            }
+            const int sp = rs_stop;
             if (sp >= 0) {
               stop_pass = sp;
               break;
@@ -1040,22 +1071,18 @@ __global__ void __launch_bounds__(P::NW * 32, P::NW <= 8 ? 2 : 1) rr_kernel(cons
           left -= S;
           done += S;
           if (threadIdx.x == 0) {
-            const int slot = q % kRecRing;
-            if (tile_changed) atomicAdd(L.rec_chg + slot, 1);
-            const unsigned old = atom_add_acq_rel_u32(reinterpret_cast<unsigned *>(L.rec_done + slot), 1u);
-            if (old == (unsigned)(ntiles - 1)) {
-              // the last tile of pass q: every other tile's change count came
-              // before its release on done, which this acquire has seen
-              const unsigned c = ld_acquire_u32(reinterpret_cast<const unsigned *>(L.rec_chg + slot));
-              L.rec_chg[slot] = 0;
-              L.rec_done[slot] = 0;
-              st_release_u32(L.rec_res + slot, ((unsigned)(q + 1) << 2) | (c ? 1u : 2u));
-            }
+            // acq_rel: the last tile's read of the word synchronises with
+            // every tile's vote on it (and what came before the votes)
+            vote_mine = tile_changed ? 1u : 0u;
+            vote_old = atom_add_acq_rel_u32(reinterpret_cast<unsigned *>(L.rec_done + q % kRecRing),
+                                            1u | (vote_mine << 16));
+            vote_pass = q;
           }
           if (left <= 0) {
             // the step cap: this pass's outcome decides between a fixed point
             // and GEO_ERR_NOT_CONVERGED (every tile reaches the cap together)
             if (threadIdx.x == 0) {
+              settle_vote();
               int sp = -1;
               const unsigned long long t0 = globaltimer_ns();
               unsigned spins = 0;
@@ -1077,6 +1104,9 @@ __global__ void __launch_bounds__(P::NW * 32, P::NW <= 8 ? 2 : 1) rr_kernel(cons
             break;
           }
         }
+        // every outcome this tile acted on was published with a release; the
+        // fence orders the reads that saw them before the stores to out
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         if (!aborted) R::store(w, L.out, L.out, false, L.H, L.W, ty0, tx0, K, TH, TW, lane, warp);
         if (L.steps_out && t == 0 && threadIdx.x == 0) {
           const int64_t applied = (int64_t)(stop_pass + 1) * K;
