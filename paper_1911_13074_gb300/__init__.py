@@ -300,10 +300,15 @@ def device_status(device=None) -> int:
     words (the library's and the no-allocation chain's): 0 or the first
     device-side error recorded since the last read."""
     lib = load()
-    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
-    with torch.cuda.device(dev):
-        v = ctypes.c_int(0)
-        rc = lib.geo_device_status(torch.cuda.current_stream(dev).cuda_stream, ctypes.byref(v))
+    cur = torch.cuda.current_device()
+    dev = torch.device("cuda", cur) if device is None else torch.device(device)
+    v = ctypes.c_int(0)
+    if dev.index in (None, cur) and _raw_stream is not None:
+        # the current device: no device switch, the raw stream handle
+        rc = lib.geo_device_status(_raw_stream(cur), ctypes.byref(v))
+    else:
+        with torch.cuda.device(dev):
+            rc = lib.geo_device_status(torch.cuda.current_stream(dev).cuda_stream, ctypes.byref(v))
     _check(rc, "geo_device_status")
     return int(v.value)
 
