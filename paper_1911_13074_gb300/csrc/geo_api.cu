@@ -390,6 +390,10 @@ HostFault host_fault() {
 
 int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64_t H, int64_t W, int64_t pitch,
                   int conn, int op, int mode, int64_t steps, int64_t *steps_out, void *stream, int batch) {
+  // rank codes run as float32 (same kernels and planes) and may take the
+  // tagged hand-over in the default shape
+  const bool rank_codes = (dt == GEO_R32);
+  if (rank_codes) dt = GEO_F32;
   const HostFault fault = host_fault();
   if (fault == FAULT_BADARG) return GEO_ERR_ARG;
   if (batch < 1) return GEO_ERR_ARG;
@@ -426,7 +430,7 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
   const bool rr = !(kern && strcmp(kern, "tile") == 0) || dt == GEO_D32;  // the distances have no tile kernel
   Plan P;
   const int code = mode == MODE_REC ? 2 + op : (mask ? op : 4 + op);
-  rc = rr ? make_plan_rr(dt, op, code, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P, batch, true)
+  rc = rr ? make_plan_rr(dt, op, code, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P, batch, !rank_codes)
           : make_plan(dt, op, conn, H, W, mode == MODE_CHAIN ? steps : 0, ds->nsm, &P, batch);
   if (rc != GEO_OK) return rc;
 
@@ -444,18 +448,21 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
     if (alias && (np & 1)) ++np;  // pass 0 must not write the buffer it reads
     if (np > INT_MAX) return GEO_ERR_ARG;  // TileLaunch::npasses is an int
   }
-  // uint8 chains of several passes with one tile per CTA hand the passes
-  // over in two zeroed planes of tagged words (GEOMORPH_TAGGED=0: plain
-  // planes and tile epochs); the lane's 4 columns must be whole words. From
-  // 3 passes on: zeroing the planes costs about as much as one hand-over saves.
-  // Reconstruction of several tiles, one per CTA, hands over the same way
-  // and finds its fixed point without a grid barrier (rr_kernel).
+  // uint8 and rank-code chains of several passes with one tile per CTA hand
+  // the passes over in two zeroed planes of tagged words (GEOMORPH_TAGGED=0:
+  // plain planes and tile epochs); the lane's 4 columns must be whole words.
+  // From 3 passes on: zeroing the planes costs about as much as one
+  // hand-over saves. Reconstruction of several tiles, one per CTA, hands
+  // over the same way and finds its fixed point without a grid barrier
+  // (rr_kernel). uint8 words: 8 bytes per 4 pixels; rank-code words: 4 bytes
+  // per pixel, rows padded to 4 words (16-byte accesses).
   const char *tg = getenv("GEOMORPH_TAGGED");
-  const bool tagged = rr && dt == GEO_U8 && batch == 1 &&
+  const bool tagged = rr && (dt == GEO_U8 || (rank_codes && P.variant == 0)) && batch == 1 &&
                       ((mode == MODE_CHAIN && np >= kTaggedMinPasses) || (mode == MODE_REC && ntiles >= 2)) &&
                       ntiles <= (size_t)P.grid && P.K % 4 == 0 && P.TW % 4 == 0 && !(tg && strcmp(tg, "0") == 0);
-  const int64_t tpitch = (W + 3) / 4;
-  const size_t tag_b = tagged ? ((2 * (size_t)tpitch * (size_t)H * 8 + 255) / 256) * 256 : 0;
+  const int64_t tpitch = rank_codes ? (W + 3) / 4 * 4 : (W + 3) / 4;
+  const size_t tword_b = rank_codes ? 4 : 8;
+  const size_t tag_b = tagged ? ((2 * (size_t)tpitch * (size_t)H * tword_b + 255) / 256) * 256 : 0;
   const size_t scratch_b = ctl_b + tag_b + (size_t)spitch_b * (size_t)H * (size_t)batch;
   // A register-kernel chain of one pass (a single-tile image, or a short
   // chain) reads the marker and writes out once: no ping-pong image, no

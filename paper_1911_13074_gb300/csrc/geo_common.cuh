@@ -14,6 +14,15 @@ enum Mode : int { MODE_CHAIN = 0, MODE_REC = 1 };
 // Internal element type next to geo_dtype: int32 distances held as u16
 // lanes (the eta iteration of the quasi-distance transform, geo_qdt.cu).
 constexpr int GEO_D32 = 3;
+// Internal element type of the float64 rank transform (geo_rank.cu): float32
+// planes whose values are rank codes, non-negative finite floats whose 7 low
+// bits are zero (rank_code). The float32 kernel computes on them unchanged;
+// the 7 free bits let its passes hand over in tagged 32-bit words.
+constexpr int GEO_R32 = 4;
+// rank r <-> its code's bit pattern: (r + 2^16) << 7 is a normal positive
+// float (no subnormals) below +inf for every r < kMaxRankCodes
+constexpr uint32_t kRankCodeBase = 1u << 16;
+constexpr int64_t kMaxRankCodes = (int64_t)(0x7f800000u >> 7) - kRankCodeBase;
 
 constexpr int kThreads = 256;  // threads per CTA of the tile kernels
 
@@ -97,13 +106,14 @@ struct TileLaunch {
   unsigned long long wait_ns;  // limit of every wait on another CTA
   int fault;              // injected failure (GEOMORPH_FAULT=timeout): the waits on other CTAs
                           // wait for something that never happens, expire and report GEO_ERR_TIMEOUT
-  // register kernel, uint8 chains with one tile per CTA: the passes hand
-  // their results over in two planes of tagged words (4 pixels + the number
-  // of the pass that wrote them) instead of plain planes plus tile epochs;
-  // nullptr: off
+  // register kernel, uint8 and rank-code chains with one tile per CTA: the
+  // passes hand their results over in two planes of tagged words instead of
+  // plain planes plus tile epochs; nullptr: off. uint8: 64-bit words of 4
+  // pixels + the number of the pass that wrote them; rank codes: 32-bit
+  // words of one code with that number modulo 128 in its 7 low bits
   unsigned long long *tagged;
-  int64_t tpitch, tplane;  // words per row / per plane of `tagged`
-  // register kernel, uint8 reconstruction with tagged planes (one tile per
+  int64_t tpitch, tplane;  // words per row / per plane of `tagged` (in the element's tagged words)
+  // register kernel, uint8 and rank-code reconstruction with tagged planes (one tile per
   // CTA): per-pass words in a ring of kRecRing slots, zeroed with the control
   // words: the votes (tiles done with the pass in the low 16 bits, tiles
   // whose interior changed in the pass's last step in the high 16), the

@@ -57,11 +57,13 @@ static int occupancy_impl(int op, int conn, size_t smem, int *bps) {
                                                                                                 : GEO_ERR_CUDA;
 }
 
-template <template <int> class RP>
+// TAGGABLE: whether the TAG instantiation exists for this shape (every
+// uint8 shape; of float32, the default shape, which rank-code planes use)
+template <template <int> class RP, bool TAGGABLE = RR<RP<DILATE>>::kTagged>
 static void *rr_kernel_ptr(int op, int conn, bool tagged = false) {
-  // RP is one of the single-image policies SU8 / SF32 / SF64; uint8 chains
-  // with tagged planes take the TAG instantiation
-  if constexpr (RR<RP<DILATE>>::kTagged) {
+  // RP is one of the single-image policies SU8 / SF32 / SF64; chains with
+  // tagged planes take the TAG instantiation
+  if constexpr (TAGGABLE) {
     if (tagged) {
       if (op == DILATE)
         return conn == 8 ? (void *)rr_kernel<RP<DILATE>, 8, true> : (void *)rr_kernel<RP<DILATE>, 4, true>;
@@ -72,9 +74,10 @@ static void *rr_kernel_ptr(int op, int conn, bool tagged = false) {
   return conn == 8 ? (void *)rr_kernel<RP<ERODE>, 8> : (void *)rr_kernel<RP<ERODE>, 4>;
 }
 
-template <template <int> class RP>
+template <template <int> class RP, bool TAGGABLE = RR<RP<DILATE>>::kTagged>
 static int launch_rr_impl(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid) {
-  void *k = rr_kernel_ptr<RP>(op, conn, L.tagged != nullptr);
+  if (L.tagged != nullptr && !TAGGABLE) return GEO_ERR_ARG;
+  void *k = rr_kernel_ptr<RP, TAGGABLE>(op, conn, L.tagged != nullptr);
   const size_t smem = rr_smem_bytes<RP<DILATE>>();
   if (set_smem_limit(k, (int)smem) != cudaSuccess)
     return GEO_ERR_CUDA;

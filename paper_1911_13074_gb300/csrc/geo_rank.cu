@@ -5,10 +5,13 @@
 // the marker's neighbourhood and of the mask), so replacing every value by
 // its rank among the distinct values of marker and mask - an order
 // isomorphism - and mapping the result back gives exactly the same image.
-// With at most 2^24 distinct values the ranks are exact float32 integers, and
-// the chain runs in the float32 register kernel (three-input max.f32 at the
-// full 32-bit rate) instead of on int64 keys (max.s64 emulated at about a
-// fifth of that rate).
+// Each rank r goes into the chain as a rank code, the float32 whose bit
+// pattern is (r + 2^16) << 7: positive, normal and finite for every r below
+// kMaxRankCodes (about 2^24), ordered as the ranks, with 7 low bits that are
+// always zero. The chain runs in the float32 register kernel (three-input
+// max.f32 at the full 32-bit rate) instead of on int64 keys (max.s64
+// emulated at about a fifth of that rate), and its passes can hand over in
+// 32-bit words that carry a pass tag in those 7 bits (GEO_R32).
 //
 //   keys    order-preserving 64-bit keys of marker and mask (the int64 key of
 //           the float64 path with the sign bit flipped, so that unsigned order
@@ -27,7 +30,7 @@
 //   unique  flags where a key differs from its predecessor, one scan: the
 //           rank of every sorted key; the distinct keys compacted and every
 //           rank written back to its pixel's position
-//   chain   float32 chain / window / reconstruction on the ranks
+//   chain   float32 chain / window / reconstruction on the rank codes
 //   unmap   out = the distinct key at the result's rank, as float64
 #include <cstdlib>
 #include <cstring>
@@ -364,17 +367,17 @@ __global__ void rk_scan_add(uint32_t *__restrict__ v, int64_t n, const uint32_t 
 
 // After the scan of the run-start flags (exclusive): the rank of sorted key i
 // among the distinct keys is scan[i] + flag[i] - 1. The run starts go to
-// uniq[rank], and every rank to the key's position: ranks[pos[i]] (marker
-// then mask, as the keys were laid out).
+// uniq[rank], and every rank's code to the key's position: codes[pos[i]]
+// (marker then mask, as the keys were laid out).
 __global__ void rk_finish(const uint64_t *__restrict__ s, const uint32_t *__restrict__ pos,
                           const uint32_t *__restrict__ flags_scan, int64_t n, uint64_t *__restrict__ uniq,
-                          float *__restrict__ ranks) {
+                          float *__restrict__ codes) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t k = s[i];
     const bool start = (i == 0 || k != s[i - 1]);
     const uint32_t r = flags_scan[i] + (start ? 1u : 0u) - 1u;
     if (start) uniq[r] = k;
-    ranks[pos[i]] = (float)r;
+    codes[pos[i]] = __uint_as_float((r + kRankCodeBase) << 7);
   }
 }
 
@@ -383,7 +386,7 @@ __global__ void rk_unmap(const float *__restrict__ r, int64_t H, int64_t W, cons
   const int64_t n = H * W;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t y = i / W, x = i - y * W;
-    out[y * pitch + x] = kdouble(uniq[(uint32_t)r[i]]);
+    out[y * pitch + x] = kdouble(uniq[(__float_as_uint(r[i]) >> 7) - kRankCodeBase]);
   }
 }
 
@@ -410,7 +413,7 @@ bool rank_path_applies(int64_t H, int64_t W, bool has_mask, int mode, int64_t st
   const char *e = getenv("GEOMORPH_F64");
   if (e && strcmp(e, "keys") == 0) return false;
   const int64_t n = H * W * (has_mask ? 2 : 1);
-  if (n > ((int64_t)1 << 24)) return false;  // ranks must stay exact float32 integers
+  if (n > kMaxRankCodes) return false;  // every rank code must stay below +inf
   if (e && strcmp(e, "ranks") == 0) return true;
   // The transform costs about 0.45 ms at 1024^2 (radix sort, ranks, map
   // back); a step there takes about 3.8 us on int64 keys and 0.7 us on the
@@ -498,7 +501,7 @@ int run_chain_ranked(const double *marker, const double *mask, double *out, int6
     }
   }
   if (rc == GEO_OK)
-    rc = run_chain_any(GEO_F32, rm, mask ? rk : nullptr, ro, H, W, W, conn, op, mode, steps, steps_out, stream, 1);
+    rc = run_chain_any(GEO_R32, rm, mask ? rk : nullptr, ro, H, W, W, conn, op, mode, steps, steps_out, stream, 1);
   if (rc == GEO_OK) {
     rk_unmap<<<ew_grid(npx), 256, 0, s>>>(ro, H, W, uniq, out, pitch);
     if (cudaGetLastError() != cudaSuccess) rc = GEO_ERR_CUDA;

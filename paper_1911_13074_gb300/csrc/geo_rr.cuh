@@ -34,6 +34,8 @@
 // step and never reaches the tile interior, which is K pixels in.
 #pragma once
 
+#include <type_traits>
+
 #include "geo_tile.cuh"
 
 namespace geo {
@@ -346,6 +348,23 @@ __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p) {
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+// 16-byte relaxed accesses at gpu scope: four 32-bit elements, each one
+// single-copy atomic (a tagged rank-code word is read whole)
+__device__ __forceinline__ uint4 ld_relaxed_v4(const unsigned *p) {
+  uint4 v;
+  asm volatile("ld.relaxed.gpu.global.v4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_v4(unsigned *p, uint4 v) {
+  asm volatile("st.relaxed.gpu.global.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
+               "r"(v.w)
+               : "memory");
+}
+// a register word's bits (uint8 pairs and distances are words already)
+__device__ __forceinline__ uint32_t word_bits(uint32_t x) { return x; }
+__device__ __forceinline__ uint32_t word_bits(float x) { return __float_as_uint(x); }
 
 // Policies of the single-image kernel (the batch kernel uses the defaults).
 // Taller bands put more work between a warp's arrival and its wait at the
@@ -702,14 +721,29 @@ struct RR {
   // fence, epoch flag or second round trip stands between a pass's stores
   // and the next pass's loads of the neighbouring tiles.
   static constexpr bool kTagged = (B == 2 && CW == 4 && sizeof(G) == 1);
+  // Rank codes (the float32 policy on GEO_R32 planes): one code per 32-bit
+  // word with the pass number modulo 128 in its 7 low bits, which every code
+  // and both infinities (the identities) leave zero. Same bytes as a plain
+  // float32 plane. The host enables it for rank-code planes only.
+  static constexpr bool kTagged32 = std::is_same<Wd, float>::value && B == 1 && CW == 4;
+  static constexpr bool kTaggable = kTagged || kTagged32;
+  using TagW = std::conditional_t<kTagged32, unsigned, unsigned long long>;
+  // tags are compared modulo kTagMask + 1 (readers want tag p while older
+  // words carry p - 2 or less, so 7 bits suffice); an injected timeout waits
+  // for a tag no pass writes in time
+  static constexpr unsigned kTagMask = kTagged32 ? 127u : 0xffffffffu;
+  static constexpr unsigned kFaultTag = kTagged32 ? 64u : (1u << 28);
+  __device__ static TagW *tplane(const TileLaunch &L, int i) {
+    return reinterpret_cast<TagW *>(L.tagged) + (size_t)i * L.tplane;
+  }
 
   // Store the interior words of the lane with tag `tag`. The lane's columns
   // are whole words: K and TW are multiples of 4, so gx is. Cells past the
   // right image border hold the identity and are stored with their word.
-  __device__ static void store_tagged(const Wd (&w)[RW][CW], unsigned long long *T, int64_t tpitch, int64_t H,
-                                      int64_t W, int64_t ty0, int64_t tx0, int K, int TH, int TW, unsigned tag,
-                                      int lane, int warp) {
-    static_assert(kTagged, "tagged planes hold uint8 pixels");
+  __device__ static void store_tagged(const Wd (&w)[RW][CW], TagW *T, int64_t tpitch, int64_t H, int64_t W,
+                                      int64_t ty0, int64_t tx0, int K, int TH, int TW, unsigned tag, int lane,
+                                      int warp) {
+    static_assert(kTaggable, "tagged planes hold uint8 pixels or rank codes");
     const int X = lane * CW;
     if (X < K || X + CW > K + TW) return;
     const int64_t gx = tx0 + (X - K);
@@ -722,10 +756,17 @@ struct RR {
         if (Y < K || Y >= K + TH) continue;
         const int64_t gy = ty0 + (Y - K);
         if (gy >= H) continue;
-        uint32_t px = 0;
+        if constexpr (kTagged32) {
+          // the lane's 4 words (gx a multiple of 4; the row pitch a multiple
+          // of 4 words, so columns past W up to it are written too)
+          st_relaxed_v4(T + gy * tpitch + gx, make_uint4(word_bits(w[r][0]) | tag, word_bits(w[r][1]) | tag,
+                                                         word_bits(w[r][2]) | tag, word_bits(w[r][3]) | tag));
+        } else {
+          uint32_t px = 0;
 #pragma unroll
-        for (int c = 0; c < CW; ++c) px |= (P::get(w[r][c], b) & 0xffu) << (8 * c);
-        st_relaxed_u64(T + gy * tpitch + (gx >> 2), ((unsigned long long)tag << 32) | px);
+          for (int c = 0; c < CW; ++c) px |= (P::get(w[r][c], b) & 0xffu) << (8 * c);
+          st_relaxed_u64(T + gy * tpitch + (gx >> 2), ((unsigned long long)tag << 32) | px);
+        }
       }
     }
   }
@@ -736,20 +777,101 @@ struct RR {
   struct NeverStop {
     __device__ bool operator()() const { return false; }
   };
-  __device__ static bool load_tagged(const unsigned long long *T, int64_t tpitch, int64_t H, int64_t W, int64_t gy0,
-                                     int64_t gx, unsigned tag, unsigned long long limit_ns, Wd (&w)[RW][CW]) {
+  __device__ static bool load_tagged(const TagW *T, int64_t tpitch, int64_t H, int64_t W, int64_t gy0, int64_t gx,
+                                     unsigned tag, unsigned long long limit_ns, Wd (&w)[RW][CW]) {
     NeverStop never;
     return load_tagged_or_stop(T, tpitch, H, W, gy0, gx, tag, limit_ns, w, never) == 1;
   }
 
   // The same, but while waiting the lane also asks `stop` now and then; when
-  // it answers true the lane gives up and leaves w as it was. 1 = loaded,
-  // 0 = the wait expired, 2 = stopped.
+  // it answers true the lane gives up. 1 = loaded, 0 = the wait expired, 2 =
+  // stopped. A stopped lane's interior cells (those its tile stores) hold
+  // its tile's own words of the previous pass: uint8 keeps w as it was (the
+  // registers that were stored), rank codes load in place, and a tile's own
+  // words are visible to it before the next pass (a CTA barrier stands
+  // between its stores and its loads), so they arrive with the tag wanted.
   template <class Stop>
-  __device__ static int load_tagged_or_stop(const unsigned long long *T, int64_t tpitch, int64_t H, int64_t W,
-                                            int64_t gy0, int64_t gx, unsigned tag, unsigned long long limit_ns,
-                                            Wd (&w)[RW][CW], const Stop &stop) {
-    static_assert(kTagged, "tagged planes hold uint8 pixels");
+  __device__ static int load_tagged_or_stop(const TagW *T, int64_t tpitch, int64_t H, int64_t W, int64_t gy0,
+                                            int64_t gx, unsigned tag, unsigned long long limit_ns, Wd (&w)[RW][CW],
+                                            const Stop &stop) {
+    static_assert(kTaggable, "tagged planes hold uint8 pixels or rank codes");
+    if constexpr (kTagged32) {
+      return load_tagged32(T, tpitch, H, W, gy0, gx, tag, limit_ns, w, stop);
+    } else {
+      return load_tagged64(T, tpitch, H, W, gy0, gx, tag, limit_ns, w, stop);
+    }
+  }
+
+  // rank codes: the lane's 4 words of each of its rows in one 16-byte load,
+  // straight into w (no second copy of the region in registers), the tags
+  // checked per word and then cleared
+  template <class Stop>
+  __device__ static int load_tagged32(const unsigned *T, int64_t tpitch, int64_t H, int64_t W, int64_t gy0,
+                                      int64_t gx, unsigned tag, unsigned long long limit_ns, Wd (&w)[RW][CW],
+                                      const Stop &stop) {
+    constexpr int NR = RW;  // one band
+    const bool cols = gx >= 0 && gx < W;
+    const unsigned *col = T + (cols ? gx : 0);
+    unsigned in = 0;
+    auto fetch = [&](int i) {
+      const uint4 v = ld_relaxed_v4(col + (gy0 + i) * tpitch);
+      w[i][0] = __uint_as_float(v.x);
+      w[i][1] = __uint_as_float(v.y);
+      w[i][2] = __uint_as_float(v.z);
+      w[i][3] = __uint_as_float(v.w);
+    };
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+      const int64_t gy = gy0 + i;
+      if (cols && gy >= 0 && gy < H) {
+        fetch(i);
+        in |= 1u << i;
+      }
+    }
+    int res = 1;
+    unsigned n = 0;
+    unsigned long long t0 = 0;
+    for (;;) {
+      unsigned miss = 0;
+#pragma unroll
+      for (int i = 0; i < NR; ++i) {
+        const uint32_t d = (word_bits(w[i][0]) ^ tag) | (word_bits(w[i][1]) ^ tag) | (word_bits(w[i][2]) ^ tag) |
+                           (word_bits(w[i][3]) ^ tag);
+        if (((in >> i) & 1u) && (d & kTagMask) != 0u) miss |= 1u << i;
+      }
+      if (!miss) break;
+      if (n == 0) t0 = globaltimer_ns();
+      if ((++n & 15u) == 0) {
+        if (stop()) {
+          res = 2;
+          break;
+        }
+        if (globaltimer_ns() - t0 > limit_ns) {
+          res = 0;
+          break;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NR; ++i)
+        if ((miss >> i) & 1u) fetch(i);
+    }
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+#pragma unroll
+      for (int c = 0; c < CW; ++c) {
+        const bool cin = ((in >> r) & 1u) && gx + c < W;
+        w[r][c] = cin ? __uint_as_float(word_bits(w[r][c]) & ~kTagMask) : P::ident();
+      }
+    }
+    return res;
+  }
+
+  // uint8: 64-bit words of 4 pixels and a 32-bit tag, loaded into a copy so
+  // that a stopped lane keeps w
+  template <class Stop>
+  __device__ static int load_tagged64(const unsigned long long *T, int64_t tpitch, int64_t H, int64_t W, int64_t gy0,
+                                      int64_t gx, unsigned tag, unsigned long long limit_ns, Wd (&w)[RW][CW],
+                                      const Stop &stop) {
     constexpr int NR = B * RW;
     const bool cols = gx >= 0 && gx < W;
     const unsigned long long *col = T + (cols ? (gx >> 2) : 0);
@@ -881,15 +1003,21 @@ struct RecStop {
 
 // Observer of a pass's last step: whether any pixel of the tile's interior
 // (and inside the image) changed. colmask: the lane's interior columns (bit
-// c); rowmask[r]: the interior rows among the two u16 lanes of word row r.
+// c); rowmask[r]: the interior rows among the two u16 lanes of word row r
+// (uint8), or bit r of rowmask[0] for an interior word row (rank codes).
 template <class P>
 struct InteriorChange {
+  static constexpr int NM = P::BANDS == 2 ? P::RW : 1;
   uint32_t colmask;
-  uint32_t rowmask[P::RW];
+  uint32_t rowmask[NM];  // one band (rank codes): bit r of rowmask[0] for word row r
   bool changed;
   template <class Wd>
   __device__ __forceinline__ void operator()(int r, int c, Wd old, Wd nv) {
-    if ((colmask >> c) & 1u) changed |= ((old ^ nv) & rowmask[r]) != 0u;
+    if constexpr (P::BANDS == 2) {
+      if ((colmask >> c) & 1u) changed |= ((word_bits(old) ^ word_bits(nv)) & rowmask[r]) != 0u;
+    } else {
+      if (((colmask >> c) & (rowmask[0] >> r) & 1u) != 0u) changed |= word_bits(old) != word_bits(nv);
+    }
   }
 };
 
@@ -899,14 +1027,14 @@ constexpr size_t rr_smem_bytes() {
 }
 
 // TAG: the variant whose chains hand the passes over in tagged planes
-// (uint8, one tile per CTA; TileLaunch::tagged). A separate instantiation,
-// so that the plain kernel's code is not touched by it.
+// (uint8 or rank codes, one tile per CTA; TileLaunch::tagged). A separate
+// instantiation, so that the plain kernel's code is not touched by it.
 // Blocks of 8 warps or fewer (the smaller shape variants) are bounded to
 // 128 registers a thread, so that two of them fit on one SM.
 template <class P, int CONN, bool TAG = false>
 __global__ void __launch_bounds__(P::NW * 32, P::NW <= 8 ? 2 : 1) rr_kernel(const TileLaunch L) {
   using R = RR<P>;
-  static_assert(!TAG || R::kTagged, "tagged planes hold uint8 pixels");
+  static_assert(!TAG || R::kTaggable, "tagged planes hold uint8 pixels or rank codes");
   using Wd = typename P::Wd;
   constexpr int CW = R::CW, RW = R::RW, NW = R::NW, PH = R::PH, RWID = R::RWID;
   // boundary-row exchange buffer [parity][warp slot][top/bottom][column], in
@@ -922,8 +1050,8 @@ __global__ void __launch_bounds__(P::NW * 32, P::NW <= 8 ? 2 : 1) rr_kernel(cons
   const bool rec = (L.mode == MODE_REC);
   const bool virt = (L.mask.ptr == nullptr);
   const bool mask_resident = (ntiles <= (int)gridDim.x);
-  // tagged hand-over between passes (one tile per CTA, uint8): chains, and
-  // reconstruction in its own loop below
+  // tagged hand-over between passes (one tile per CTA, uint8 or rank codes):
+  // chains, and reconstruction in its own loop below
   const bool tagged = TAG && L.tagged != nullptr && mask_resident;
 
   __shared__ __align__(8) uint64_t xbar;  // split-phase step barrier of the whole CTA
@@ -970,15 +1098,24 @@ __global__ void __launch_bounds__(P::NW * 32, P::NW <= 8 ? 2 : 1) rr_kernel(cons
           const int X = lane * CW + c;
           if (X >= K && X < K + TW && tx0 + (X - K) < L.W) ic.colmask |= 1u << c;
         }
+        if constexpr (R::B == 2) {
 #pragma unroll
-        for (int r = 0; r < RW; ++r) {
-          uint32_t rm = 0;
+          for (int r = 0; r < RW; ++r) {
+            uint32_t rm = 0;
 #pragma unroll
-          for (int b = 0; b < R::B; ++b) {
-            const int Y = warp * PH + b * RW + r;
-            if (Y >= K && Y < K + TH && ty0 + (Y - K) < L.H) rm |= 0xffffu << (16 * b);
+            for (int b = 0; b < R::B; ++b) {
+              const int Y = warp * PH + b * RW + r;
+              if (Y >= K && Y < K + TH && ty0 + (Y - K) < L.H) rm |= 0xffffu << (16 * b);
+            }
+            ic.rowmask[r] = rm;
           }
-          ic.rowmask[r] = rm;
+        } else {
+          ic.rowmask[0] = 0;
+#pragma unroll
+          for (int r = 0; r < RW; ++r) {
+            const int Y = warp * PH + r;
+            if (Y >= K && Y < K + TH && ty0 + (Y - K) < L.H) ic.rowmask[0] |= 1u << r;
+          }
         }
         int chk = 0, stop_pass = -1;
         bool aborted = false;
@@ -1013,9 +1150,9 @@ __global__ void __launch_bounds__(P::NW * 32, P::NW <= 8 ? 2 : 1) rr_kernel(cons
             // this pass's region: the previous pass's words of this tile and
             // its neighbours, unless the fixed point becomes known meanwhile
             RecStop stop{&L, rs_chk};
-            const unsigned want = L.fault ? (unsigned)q + (1u << 28) : (unsigned)q;
-            const int lr = R::load_tagged_or_stop(L.tagged + (size_t)((q - 1) & 1) * L.tplane, L.tpitch, L.H, L.W,
-                                                  gy0, gx, want, L.wait_ns, w, stop);
+            const unsigned want = ((unsigned)q + (L.fault ? R::kFaultTag : 0u)) & R::kTagMask;
+            const int lr =
+                R::load_tagged_or_stop(R::tplane(L, (q - 1) & 1), L.tpitch, L.H, L.W, gy0, gx, want, L.wait_ns, w, stop);
             const int failed = __syncthreads_or(lr == 0);
             const int stopped = __syncthreads_or(lr == 2);
             if (threadIdx.x == 0) {
@@ -1066,8 +1203,8 @@ __global__ void __launch_bounds__(P::NW * 32, P::NW <= 8 ? 2 : 1) rr_kernel(cons
             aborted = true;
             break;
           }
-          R::store_tagged(w, L.tagged + (size_t)(q & 1) * L.tplane, L.tpitch, L.H, L.W, ty0, tx0, K, TH, TW,
-                          (unsigned)(q + 1), lane, warp);
+          R::store_tagged(w, R::tplane(L, q & 1), L.tpitch, L.H, L.W, ty0, tx0, K, TH, TW,
+                          (unsigned)(q + 1) & R::kTagMask, lane, warp);
           left -= S;
           done += S;
           if (threadIdx.x == 0) {
@@ -1175,9 +1312,8 @@ __global__ void __launch_bounds__(P::NW * 32, P::NW <= 8 ? 2 : 1) rr_kernel(cons
         if (tagged && pass > 0) {
           // the previous pass's words: from this tile's own threads (its
           // interior) and from the 8 neighbouring tiles (the halo)
-          const unsigned want = L.fault ? (unsigned)pass + (1u << 28) : (unsigned)pass;
-          if (!R::load_tagged(L.tagged + (size_t)((pass - 1) & 1) * L.tplane, L.tpitch, L.H, L.W, gy0, gx, want,
-                              L.wait_ns, w))
+          const unsigned want = ((unsigned)pass + (L.fault ? R::kFaultTag : 0u)) & R::kTagMask;
+          if (!R::load_tagged(R::tplane(L, (pass - 1) & 1), L.tpitch, L.H, L.W, gy0, gx, want, L.wait_ns, w))
             record_status(L.status, GEO_ERR_TIMEOUT);
           loaded = true;
         }
@@ -1210,8 +1346,8 @@ __global__ void __launch_bounds__(P::NW * 32, P::NW <= 8 ? 2 : 1) rr_kernel(cons
       bool stored = false;
       if constexpr (TAG) {
         if (tagged && pass + 1 < L.npasses) {
-          R::store_tagged(w, L.tagged + (size_t)(pass & 1) * L.tplane, L.tpitch, L.H, L.W, ty0, tx0, K, TH, TW,
-                          (unsigned)(pass + 1), lane, warp);
+          R::store_tagged(w, R::tplane(L, pass & 1), L.tpitch, L.H, L.W, ty0, tx0, K, TH, TW,
+                          (unsigned)(pass + 1) & R::kTagMask, lane, warp);
           stored = true;
         }
       }

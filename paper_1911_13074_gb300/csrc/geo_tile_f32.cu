@@ -13,7 +13,7 @@ int occupancy_tile_f32(int op, int conn, size_t smem, int *bps) { return occupan
 int launch_rr_f32(const TileLaunch &L, int op, int conn, cudaStream_t s, int grid, int variant) {
   if (variant == 1) return launch_rr_f32_v1(L, op, conn, s, grid);
   if (variant == 2) return launch_rr_f32_v2(L, op, conn, s, grid);
-  return launch_rr_impl<SF32>(L, op, conn, s, grid);
+  return launch_rr_impl<SF32, true>(L, op, conn, s, grid);  // with the tagged form for rank codes
 }
 
 int occupancy_rr_f32(int op, int conn, int *bps, int variant) {
