@@ -15,19 +15,18 @@
 //
 //   keys    order-preserving 64-bit keys of marker and mask (the int64 key of
 //           the float64 path with the sign bit flipped, so that unsigned order
-//           is numeric order; -0.0 sorts below +0.0, as there), each with its
-//           position, and in the same pass the global histograms of all
-//           eight 8-bit digits
+//           is numeric order; -0.0 sorts below +0.0, as there), and in the
+//           same pass the global histograms of all eight 8-bit digits
 //   sort    least-significant-digit radix sort of (key, position), 8 passes
-//           of one kernel each: a block takes the next tile by ticket, ranks
-//           its keys by digit in position order (warps group equal digits
-//           by one shared-memory bit per lane), publishes its digit counts
-//           and finds the
-//           counts of the tiles before it by decoupled look-back (bounded
-//           waits), orders the tile by digit in shared memory and writes
-//           each digit's run where the global histogram and the look-back
-//           put it
-//   unique  flags where a key differs from its predecessor, one scan: the
+//           of one kernel each (the first takes each key's position from its
+//           index): a block takes the next tile by ticket, ranks its keys by
+//           digit in position order (warps group equal digits by one
+//           shared-memory bit per lane), publishes its digit counts and
+//           finds the counts of the tiles before it by decoupled look-back
+//           (bounded waits), orders the tile by digit in shared memory and
+//           writes each digit's run where the global histogram (scanned by
+//           every block) and the look-back put it
+//   unique  one scan of the flags "key differs from its predecessor": the
 //           rank of every sorted key; the distinct keys compacted and every
 //           rank written back to its pixel's position
 //   chain   float32 chain / window / reconstruction on the rank codes
@@ -60,46 +59,44 @@ __device__ __forceinline__ double kdouble(uint64_t u) {
   return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
 }
 
-// keys[0 .. H*W) = marker, keys[H*W .. 2 H*W) = mask (when given), pos[i] =
-// i, and hist[p * 256 + d] += the keys whose digit p (bits 8p .. 8p + 7) is d
+// keys[0 .. H*W) = marker, keys[H*W .. 2 H*W) = mask (when given), and
+// hist[p * 256 + d] += the keys whose digit p (bits 8p .. 8p + 7) is d. The
+// high digits of real data take few values (sign and exponent), so the lanes
+// of a warp whose digit equals lane 0's add to it with one atomic: one
+// shared-memory address hit by all 32 lanes would serialise.
 __global__ void __launch_bounds__(256) rk_keys(const double *__restrict__ a, const double *__restrict__ b, int64_t H,
                                                int64_t W, int64_t pitch, uint64_t *__restrict__ keys,
-                                               uint32_t *__restrict__ pos, uint32_t *__restrict__ hist) {
+                                               uint32_t *__restrict__ hist) {
   __shared__ uint32_t h[kPasses * kDigits];
   for (int i = threadIdx.x; i < kPasses * kDigits; i += blockDim.x) h[i] = 0;
   __syncthreads();
   const int64_t npx = H * W, n = b ? 2 * npx : npx;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = i < npx ? i : i - npx;
-    const int64_t y = j / W, x = j - y * W;
-    const uint64_t k = dkey(i < npx ? a[y * pitch + x] : b[y * pitch + x]);
-    keys[i] = k;
-    pos[i] = (uint32_t)i;
+  const int lane = threadIdx.x & 31;
+  // the loop is uniform per block, so every lane takes part in the votes
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + threadIdx.x;
+    const bool valid = i < n;
+    uint64_t k = 0;
+    if (valid) {
+      const int64_t j = i < npx ? i : i - npx;
+      const int64_t y = j / W, x = j - y * W;
+      k = dkey(i < npx ? a[y * pitch + x] : b[y * pitch + x]);
+      keys[i] = k;
+    }
 #pragma unroll
-    for (int p = 0; p < kPasses; ++p) atomicAdd(&h[p * kDigits + (int)((k >> (8 * p)) & 255u)], 1u);
+    for (int p = 0; p < kPasses; ++p) {
+      const unsigned d = valid ? (unsigned)((k >> (8 * p)) & 255u) : 256u;
+      const unsigned lead = __shfl_sync(0xffffffffu, d, 0);
+      const unsigned same = __ballot_sync(0xffffffffu, d == lead);
+      if (valid) {
+        if (d != lead) atomicAdd(&h[p * kDigits + (int)d], 1u);
+        else if (lane == 0) atomicAdd(&h[p * kDigits + (int)d], (unsigned)__popc(same));
+      }
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kPasses * kDigits; i += blockDim.x)
     if (h[i]) atomicAdd(&hist[i], h[i]);
-}
-
-// hist[p][d] -> exclusive prefix over d (the first output position of digit
-// d in pass p); one block of 256 threads
-__global__ void __launch_bounds__(kDigits) rk_digit_offsets(uint32_t *__restrict__ hist) {
-  __shared__ uint32_t v[kDigits];
-  for (int p = 0; p < kPasses; ++p) {
-    const uint32_t c = hist[p * kDigits + threadIdx.x];
-    v[threadIdx.x] = c;
-    __syncthreads();
-    for (int o = 1; o < kDigits; o <<= 1) {
-      const uint32_t t = threadIdx.x >= (unsigned)o ? v[threadIdx.x - o] : 0u;
-      __syncthreads();
-      v[threadIdx.x] += t;
-      __syncthreads();
-    }
-    hist[p * kDigits + threadIdx.x] = v[threadIdx.x] - c;
-    __syncthreads();
-  }
 }
 
 // Exclusive scan of n uint32 in place, one block, in chunks of kScanTile
@@ -150,7 +147,8 @@ __device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
   asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// One pass of the radix sort of (key, pos) on the digit at `shift`.
+// One pass of the radix sort of (key, pos) on the digit at `shift` (pin ==
+// nullptr: the positions are the indices, in the first pass).
 // A block takes tile t by ticket (so every tile before t belongs to a block
 // that is already running: the look-back waits always end), and warp w owns
 // keys [w * 256, (w + 1) * 256) of the tile, 8 per lane held in registers
@@ -164,10 +162,15 @@ __device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v) {
 // per-digit words: a tile's own count, or the inclusive count once the tile
 // knows it; each lane reads kLbWindow predecessors at once), so that the
 // counts of most earlier tiles are there when needed. Digit d's keys of the
-// tile then go, contiguously, to doff[d] + the sum found. A look-back wait
-// that expires (limit_ns) records GEO_ERR_TIMEOUT and the block writes
-// nothing.
-constexpr int kLbWindow = 16;
+// tile then go, contiguously, to the digit's first output position (the
+// exclusive prefix of the pass's global histogram, which every block scans
+// for itself) + the sum found. A look-back wait that expires (limit_ns)
+// records GEO_ERR_TIMEOUT and the block writes nothing.
+// 8 predecessors a read. Measured transform time at 2M keys by window: 1:
+// 0.44 ms, 2: 0.42, 4: 0.40, 8: 0.40, 16: 0.48, 32: 0.63 (the wider reads of
+// a spinning look-back take issue slots that the other blocks on the SM
+// need; pausing between them changed nothing).
+constexpr int kLbWindow = 8;
 constexpr int kOsRounds = kOsWarpKeys / 32;  // keys per lane
 
 // The lanes of the warp whose digit equals this lane's (d < 256; a lane with
@@ -188,7 +191,7 @@ __device__ __forceinline__ unsigned warp_digit_peers(uint32_t *wm, unsigned d, i
 __global__ void __launch_bounds__(kOsThreads, 4) rk_onesweep(const uint64_t *__restrict__ kin,
                                                           const uint32_t *__restrict__ pin, uint64_t *__restrict__ kout,
                                                           uint32_t *__restrict__ pout, int64_t n, int shift,
-                                                          const uint32_t *__restrict__ doff, uint32_t *lookback,
+                                                          const uint32_t *__restrict__ hist, uint32_t *lookback,
                                                           uint32_t *ticket, int *status,
                                                           unsigned long long limit_ns) {
   extern __shared__ __align__(16) char os_dyn[];
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(kOsThreads, 4) rk_onesweep(const uint64_t *__r
   uint32_t *sp = reinterpret_cast<uint32_t *>(os_dyn + 8 * kOsTile);  // and their positions
   __shared__ uint32_t cnt[kOsWarps][kDigits];
   __shared__ uint32_t wmask[kOsWarps][kDigits];  // warp_digit_peers' words
-  __shared__ uint32_t dend[kDigits], tcnt[kDigits], gbase[kDigits];
+  __shared__ uint32_t dend[kDigits], tcnt[kDigits], gbase[kDigits], doff[kDigits];
   __shared__ int tile_s, fail_s;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(kOsThreads, 4) rk_onesweep(const uint64_t *__r
   for (int r = 0; r < kOsRounds; ++r) {
     const int64_t idx = wbase + 32 * r + lane;
     k[r] = idx < n ? kin[idx] : 0ull;
-    pk[r] = idx < n ? pin[idx] : 0u;
+    pk[r] = idx < n ? (pin ? pin[idx] : (uint32_t)idx) : 0u;
   }
 #pragma unroll
   for (int r = 0; r < kOsRounds; ++r) {
@@ -241,12 +244,17 @@ __global__ void __launch_bounds__(kOsThreads, 4) rk_onesweep(const uint64_t *__r
     tcnt[d] = c;
     dend[d] = c;
     st_relaxed_u32(lookback + (int64_t)tile * kDigits + d, (tile == 0 ? kLbPre : kLbAgg) | c);
+    doff[d] = hist[d];
   }
   __syncthreads();
-  for (int o = 1; o < kDigits; o <<= 1) {  // dend[d]: the tile's keys of digits <= d
+  // inclusive scans over the digits: dend[d], the tile's keys of digits <= d;
+  // doff[d], all keys of digits <= d (made exclusive below)
+  for (int o = 1; o < kDigits; o <<= 1) {
     const uint32_t t = threadIdx.x >= (unsigned)o ? dend[threadIdx.x - o] : 0u;
+    const uint32_t u = threadIdx.x >= (unsigned)o ? doff[threadIdx.x - o] : 0u;
     __syncthreads();
     dend[threadIdx.x] += t;
+    doff[threadIdx.x] += u;
     __syncthreads();
   }
 #pragma unroll
@@ -303,7 +311,7 @@ __global__ void __launch_bounds__(kOsThreads, 4) rk_onesweep(const uint64_t *__r
       }
       st_relaxed_u32(lookback + (int64_t)tile * kDigits + d, kLbPre | (before + tcnt[d]));
     }
-    gbase[d] = doff[d] + before;
+    gbase[d] = doff[d] - hist[d] + before;  // exclusive: the first output position of digit d
   }
   __syncthreads();
   if (fail_s) {
@@ -323,23 +331,19 @@ __global__ void __launch_bounds__(kOsThreads, 4) rk_onesweep(const uint64_t *__r
   }
 }
 
-// flags[i] = 1 where sorted[i] starts a run of equal keys
-__global__ void rk_flags(const uint64_t *__restrict__ s, int64_t n, uint32_t *__restrict__ f) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    f[i] = (i == 0 || s[i] != s[i - 1]) ? 1u : 0u;
-}
-
-// Exclusive scan of large arrays: per-block scans, block sums scanned by
-// rk_scan_small, then added back.
-__global__ void __launch_bounds__(kScanThreads) rk_scan_blocks(uint32_t *__restrict__ v, int64_t n,
-                                                               uint32_t *__restrict__ sums) {
+// The run-start flags of the sorted keys (1 where a key differs from its
+// predecessor), scanned per block of kScanTile: v = the exclusive scan within
+// the block, sums = the block totals (scanned by rk_scan_small; rk_finish
+// adds them back).
+__global__ void __launch_bounds__(kScanThreads) rk_scan_blocks(const uint64_t *__restrict__ s, uint32_t *__restrict__ v,
+                                                               int64_t n, uint32_t *__restrict__ sums) {
   __shared__ uint32_t part[kScanThreads];
   const int64_t c0 = (int64_t)blockIdx.x * kScanTile;
   uint32_t loc[kScanItems], sum = 0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     const int64_t idx = c0 + (int64_t)threadIdx.x * kScanItems + i;
-    loc[i] = idx < n ? v[idx] : 0u;
+    loc[i] = idx < n ? ((idx == 0 || s[idx] != s[idx - 1]) ? 1u : 0u) : 0u;
     sum += loc[i];
   }
   part[threadIdx.x] = sum;
@@ -360,22 +364,18 @@ __global__ void __launch_bounds__(kScanThreads) rk_scan_blocks(uint32_t *__restr
   if (threadIdx.x == kScanThreads - 1) sums[blockIdx.x] = part[kScanThreads - 1];
 }
 
-__global__ void rk_scan_add(uint32_t *__restrict__ v, int64_t n, const uint32_t *__restrict__ sums) {
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx < n) v[idx] += sums[idx / kScanTile];
-}
-
-// After the scan of the run-start flags (exclusive): the rank of sorted key i
-// among the distinct keys is scan[i] + flag[i] - 1. The run starts go to
-// uniq[rank], and every rank's code to the key's position: codes[pos[i]]
-// (marker then mask, as the keys were laid out).
+// After the scan of the run-start flags (exclusive: the block's scan plus
+// the scanned block total): the rank of sorted key i among the distinct keys
+// is scan[i] + flag[i] - 1. The run starts go to uniq[rank], and every rank's
+// code to the key's position: codes[pos[i]] (marker then mask, as the keys
+// were laid out).
 __global__ void rk_finish(const uint64_t *__restrict__ s, const uint32_t *__restrict__ pos,
-                          const uint32_t *__restrict__ flags_scan, int64_t n, uint64_t *__restrict__ uniq,
-                          float *__restrict__ codes) {
+                          const uint32_t *__restrict__ flags_scan, const uint32_t *__restrict__ block_sums, int64_t n,
+                          uint64_t *__restrict__ uniq, float *__restrict__ codes) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t k = s[i];
     const bool start = (i == 0 || k != s[i - 1]);
-    const uint32_t r = flags_scan[i] + (start ? 1u : 0u) - 1u;
+    const uint32_t r = flags_scan[i] + block_sums[i / kScanTile] + (start ? 1u : 0u) - 1u;
     if (start) uniq[r] = k;
     codes[pos[i]] = __uint_as_float((r + kRankCodeBase) << 7);
   }
@@ -395,16 +395,6 @@ size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 int ew_grid(int64_t n) {
   const int64_t b = (n + 255) / 256;
   return (int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
-}
-
-// device-wide exclusive scan of n uint32; block_sums holds one entry per
-// kScanTile elements (scanned by one block in chunks)
-int scan_u32(uint32_t *v, int64_t n, uint32_t *block_sums, uint32_t *total, cudaStream_t s) {
-  const int64_t nb = (n + kScanTile - 1) / kScanTile;
-  rk_scan_blocks<<<(unsigned)nb, kScanThreads, 0, s>>>(v, n, block_sums);
-  rk_scan_small<<<1, kScanThreads, 0, s>>>(block_sums, nb, total);
-  rk_scan_add<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, n, block_sums);
-  return cudaGetLastError() == cudaSuccess ? GEO_OK : GEO_ERR_CUDA;
 }
 
 }  // namespace
@@ -430,7 +420,7 @@ int run_chain_ranked(const double *marker, const double *mask, double *out, int6
   const int64_t npx = H * W, n = npx * (mask ? 2 : 1);
   const int ntiles = (int)((n + kOsTile - 1) / kOsTile);
   const int64_t nsb = (n + kScanTile - 1) / kScanTile;
-  // scratch: [keys A][keys B][pos A][pos B][uniq][flags/scan][digit offsets][scan block sums][U]
+  // scratch: [keys A][keys B][pos A][pos B][uniq][flag scan][digit histograms][scan block sums][U]
   //          [tickets][look-back words, per pass][ranks: marker, mask][ranks out]
   const size_t kb = up256((size_t)n * 8), pb = up256((size_t)n * 4), fb = up256((size_t)n * 4);
   const size_t hb = up256((size_t)kPasses * kDigits * 4), sb = up256((size_t)(nsb > 0 ? nsb : 1) * 4);
@@ -451,7 +441,7 @@ int run_chain_ranked(const double *marker, const double *mask, double *out, int6
   p += 2 * pb;
   uint32_t *flags = (uint32_t *)p;
   p += fb;
-  uint32_t *hist = (uint32_t *)p;  // digit histograms, then offsets; zeroed with the tickets and look-back
+  uint32_t *hist = (uint32_t *)p;  // digit histograms of the 8 passes
   p += hb;
   uint32_t *bsums = (uint32_t *)p;
   p += sb;
@@ -476,10 +466,9 @@ int run_chain_ranked(const double *marker, const double *mask, double *out, int6
   const bool fault = host_fault() == FAULT_TIMEOUT;
   const unsigned long long limit = fault ? kFaultWaitNs : kWaitLimitNs;
   if (rc == GEO_OK) {
-    rk_keys<<<ew_grid(n), 256, 0, s>>>(marker, mask, H, W, pitch, ka, pa, hist);
-    rk_digit_offsets<<<1, kDigits, 0, s>>>(hist);
+    rk_keys<<<ew_grid(n), 256, 0, s>>>(marker, mask, H, W, pitch, ka, hist);
     uint64_t *ks = ka, *kd = kbuf;
-    uint32_t *ps = pa, *pd = pbuf;
+    uint32_t *ps = nullptr, *pd = pa;  // the first pass takes the positions from the indices
     for (int pass = 0; pass < kPasses; ++pass) {
       rk_onesweep<<<ntiles, kOsThreads, os_smem, s>>>(ks, ps, kd, pd, n, 8 * pass, hist + pass * kDigits,
                                                       lookback + (size_t)pass * ntiles * kDigits, tickets + pass,
@@ -487,18 +476,14 @@ int run_chain_ranked(const double *marker, const double *mask, double *out, int6
       uint64_t *t = ks;
       ks = kd;
       kd = t;
-      uint32_t *u = ps;
       ps = pd;
-      pd = u;
+      pd = (pd == pa) ? pbuf : pa;
     }
-    // 8 passes: the sorted keys and their positions are back in ka / pa (ks / ps)
-    rk_flags<<<ew_grid(n), 256, 0, s>>>(ks, n, flags);
+    // 8 passes: the sorted keys are back in ka, their positions in pbuf (ks / ps)
+    rk_scan_blocks<<<(unsigned)nsb, kScanThreads, 0, s>>>(ks, flags, n, bsums);
+    rk_scan_small<<<1, kScanThreads, 0, s>>>(bsums, nsb, U);
+    rk_finish<<<ew_grid(n), 256, 0, s>>>(ks, ps, flags, bsums, n, uniq, rm);
     if (cudaGetLastError() != cudaSuccess) rc = GEO_ERR_CUDA;
-    if (rc == GEO_OK) rc = scan_u32(flags, n, bsums, U, s);
-    if (rc == GEO_OK) {
-      rk_finish<<<ew_grid(n), 256, 0, s>>>(ks, ps, flags, n, uniq, rm);
-      if (cudaGetLastError() != cudaSuccess) rc = GEO_ERR_CUDA;
-    }
   }
   if (rc == GEO_OK)
     rc = run_chain_any(GEO_R32, rm, mask ? rk : nullptr, ro, H, W, W, conn, op, mode, steps, steps_out, stream, 1);
