@@ -63,7 +63,10 @@ __device__ __forceinline__ double kdouble(uint64_t u) {
 // hist[p * 256 + d] += the keys whose digit p (bits 8p .. 8p + 7) is d. The
 // high digits of real data take few values (sign and exponent), so the lanes
 // of a warp whose digit equals lane 0's add to it with one atomic: one
-// shared-memory address hit by all 32 lanes would serialise.
+// shared-memory address hit by all 32 lanes would serialise. (The kernel
+// is bound by its shared-memory atomics: 8 per key. Fewer blocks with 8 keys
+// a thread in flight took 51 us at 2M keys against 35 us for a block per 256
+// keys.)
 __global__ void __launch_bounds__(256) rk_keys(const double *__restrict__ a, const double *__restrict__ b, int64_t H,
                                                int64_t W, int64_t pitch, uint64_t *__restrict__ keys,
                                                uint32_t *__restrict__ hist) {
@@ -79,8 +82,8 @@ __global__ void __launch_bounds__(256) rk_keys(const double *__restrict__ a, con
     uint64_t k = 0;
     if (valid) {
       const int64_t j = i < npx ? i : i - npx;
-      const int64_t y = j / W, x = j - y * W;
-      k = dkey(i < npx ? a[y * pitch + x] : b[y * pitch + x]);
+      const int64_t o = pitch == W ? j : (j / W) * pitch + j % W;
+      k = dkey(i < npx ? a[o] : b[o]);
       keys[i] = k;
     }
 #pragma unroll
@@ -337,7 +340,9 @@ __global__ void __launch_bounds__(kOsThreads, 4) rk_onesweep(const uint64_t *__r
 // adds them back).
 __global__ void __launch_bounds__(kScanThreads) rk_scan_blocks(const uint64_t *__restrict__ s, uint32_t *__restrict__ v,
                                                                int64_t n, uint32_t *__restrict__ sums) {
-  __shared__ uint32_t part[kScanThreads];
+  static_assert(kScanThreads == 32 * 32, "one warp scans the warp totals");
+  __shared__ uint32_t wsum[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t c0 = (int64_t)blockIdx.x * kScanTile;
   uint32_t loc[kScanItems], sum = 0;
 #pragma unroll
@@ -346,22 +351,34 @@ __global__ void __launch_bounds__(kScanThreads) rk_scan_blocks(const uint64_t *_
     loc[i] = idx < n ? ((idx == 0 || s[idx] != s[idx - 1]) ? 1u : 0u) : 0u;
     sum += loc[i];
   }
-  part[threadIdx.x] = sum;
-  __syncthreads();
-  for (int o = 1; o < kScanThreads; o <<= 1) {
-    const uint32_t t = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += t;
-    __syncthreads();
+  // inclusive scan of the thread sums: within each warp by shuffles, then
+  // of the 32 warp totals by warp 0
+  uint32_t x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
-  uint32_t run = part[threadIdx.x] - sum;
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t t = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    wsum[lane] = t;
+  }
+  __syncthreads();
+  uint32_t run = (warp ? wsum[warp - 1] : 0u) + x - sum;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     const int64_t idx = c0 + (int64_t)threadIdx.x * kScanItems + i;
     if (idx < n) v[idx] = run;
     run += loc[i];
   }
-  if (threadIdx.x == kScanThreads - 1) sums[blockIdx.x] = part[kScanThreads - 1];
+  if (threadIdx.x == 0) sums[blockIdx.x] = wsum[31];
 }
 
 // After the scan of the run-start flags (exclusive: the block's scan plus
@@ -405,11 +422,12 @@ bool rank_path_applies(int64_t H, int64_t W, bool has_mask, int mode, int64_t st
   const int64_t n = H * W * (has_mask ? 2 : 1);
   if (n > kMaxRankCodes) return false;  // every rank code must stay below +inf
   if (e && strcmp(e, "ranks") == 0) return true;
-  // The transform costs about 0.45 ms at 1024^2 (radix sort, ranks, map
-  // back); a step there takes about 3.8 us on int64 keys and 0.7 us on the
-  // ranks, so the ranks pay from about 150 steps on. Reconstruction takes
-  // its chain length from the image's longer side. Small images stay on the
-  // keys (the launches of the transform dominate there).
+  // At 1024^2 a call on the rank codes costs about 0.39 ms + 0.62 us a step
+  // (radix sort, ranks, map back, the tagged float32 chain), one on int64
+  // keys about 3.2-3.8 us a step, so the ranks pay from about 140 steps on.
+  // Reconstruction takes its chain length from the image's longer side.
+  // Small images stay on the keys (the launches of the transform dominate
+  // there).
   const int64_t est = mode == MODE_REC ? (H > W ? H : W) : steps;
   return est >= 160 && H * W >= ((int64_t)1 << 16);
 }
