@@ -419,7 +419,10 @@ int run_chain_any(int dt, const void *marker, const void *mask, void *out, int64
   }
 
   // float64: long chains and reconstructions run on the ranks of the values
-  if (dt == GEO_F64 && batch == 1 && fault == FAULT_NONE && rank_path_applies(H, W, mask != nullptr, mode, steps))
+  // (an injected allocation failure is tested on the direct path; an
+  // injected timeout reaches the rank path's chain)
+  if (dt == GEO_F64 && batch == 1 && (fault == FAULT_NONE || fault == FAULT_TIMEOUT) &&
+      rank_path_applies(H, W, mask != nullptr, mode, steps))
     return run_chain_ranked((const double *)marker, (const double *)mask, (double *)out, H, W, pitch, conn, op, mode,
                             steps, steps_out, stream);
 

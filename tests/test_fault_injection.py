@@ -63,15 +63,22 @@ def test_alloc_failure_raises():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("kernel", ["rr", "rr-plain", "tile"])
+@pytest.mark.parametrize("kernel", ["rr", "rr-plain", "tile", "f64-ranks"])
 def test_timeout_is_reported_and_the_context_stays_usable(kernel, monkeypatch):
+    """f64-ranks: float64 on the rank path, whose chain and reconstruction
+    hand over in rank-code words with a 7-bit pass tag (the injected wait is
+    for a tag 64 passes away)."""
     import torch
     if kernel == "tile":
         monkeypatch.setenv("GEOMORPH_KERNEL", "tile")
     if kernel == "rr-plain":
         monkeypatch.setenv("GEOMORPH_TAGGED", "0")
+    if kernel == "f64-ranks":
+        monkeypatch.setenv("GEOMORPH_F64", "ranks")
     m = gm()
     w = synth.workload0(300, 300)
+    if kernel == "f64-ranks":
+        w = {k: v.astype(np.float64) for k, v in w.items()}
     f, g = torch.from_numpy(w["marker"]).cuda(), torch.from_numpy(w["mask"]).cuda()
     assert m.device_status() == 0
     with fault("timeout"):

@@ -208,6 +208,41 @@ def test_tagged_reconstruction_cap_and_step_count(monkeypatch):
     assert m.device_status() == 0
 
 
+def test_rank_code_reconstruction_cap_and_step_count(monkeypatch):
+    """float64 reconstruction on the rank path: the float32 kernel runs on
+    rank codes and, with several tiles (one per CTA), hands its passes over
+    in 32-bit words that carry a 7-bit pass tag, with the per-pass vote
+    instead of a grid barrier. The fixed point equals the oracle's, the
+    reported steps cover the oracle's changing steps plus the step that
+    changes nothing, and capped below its length it records
+    GEO_ERR_NOT_CONVERGED with out holding exactly the chain of the capped
+    number of steps."""
+    monkeypatch.setenv("GEOMORPH_F64", "ranks")
+    monkeypatch.delenv("GEOMORPH_TAGGED", raising=False)
+    monkeypatch.delenv("GEOMORPH_KERNEL", raising=False)
+    m = gm()
+    w = synth.workload0(300, 420)
+    rng = np.random.default_rng(0x7A6)
+    msk = w["mask"].astype(np.float64) + np.round(rng.random((300, 420)) * 4.0) / 8.0  # ties and fractions
+    f = np.minimum(w["marker"].astype(np.float64), msk)
+    K, TH, TW = m.plan_info(torch.float32, "dilate_rec", 8, 300, 420, 0)
+    assert -(-300 // TH) * -(-420 // TW) >= 2  # several tiles
+    out, steps = m.reconstruct(dev(f), dev(msk), return_steps=True)
+    ref, n = oracle.reconstruct(f, msk)
+    assert_same(host(out), ref, "rank-code reconstruction")
+    assert int(steps.item()) >= n + 1
+    for cap in (37, 2 * K + 3):
+        o = m.reconstruct(dev(f), dev(msk), max_steps=cap, check=False)
+        assert m.device_status() == -6
+        assert_same(host(o), oracle.chain(f, msk, cap), f"capped at {cap}")
+    # erosion, in place, 4-connected
+    e = msk + 40.0
+    t = dev(e)
+    m.reconstruct(t, dev(msk), conn=4, op="erode", out=t)
+    assert_same(host(t), oracle.reconstruct(e, msk, conn=4, op="erode")[0], "rank-code erosion, in place")
+    assert m.device_status() == 0
+
+
 def test_full_size_1024_u8_chain(kernel):
     """1024x1024 u8 (workload 1), 100-step chains of both operations, whole image."""
     w = synth.workload1_u8()
