@@ -180,7 +180,11 @@ __device__ __forceinline__ void keys_load(QdtKeys &q, const TileLaunch &L, const
 // Part 1. Chain of L.steps unmasked erosions of L.marker, passes of K steps
 // synchronised point to point by the per-tile epochs as in rr_kernel; the
 // image ping-pongs between L.out and L.scratch (both library scratch), the
-// keys go to Rp / Dp.
+// keys go to Rp / Dp. With one tile per CTA and L.tagged set, the passes
+// hand the image over in tagged words instead (as the uint8 chains of
+// rr_kernel do: no epochs, release fence or second round trip; the same
+// write-after-read argument holds, every tile's stores depending on its
+// tag-checked loads).
 template <int CONN>
 __global__ void __launch_bounds__(QP::NW * 32, 1) qdt_kernel(const TileLaunch L, const Plane Rp, const Plane Dp) {
   using R = RR<QP>;
@@ -192,6 +196,7 @@ __global__ void __launch_bounds__(QP::NW * 32, 1) qdt_kernel(const TileLaunch L,
   const int K = L.K, TH = L.TH, TW = L.TW;
   const int ntiles = L.tiles_x * L.tiles_y;
   const bool resident = ntiles <= (int)gridDim.x;  // one tile per CTA: keys stay in registers
+  const bool tagged = resident && L.tagged != nullptr;
 
   __shared__ __align__(8) uint64_t xbar;
   if (threadIdx.x == 0) mbar_init(&xbar, NW * 32);
@@ -216,12 +221,17 @@ __global__ void __launch_bounds__(QP::NW * 32, 1) qdt_kernel(const TileLaunch L,
       const int ty = t / L.tiles_x, tx = t - ty * L.tiles_x;
       const int64_t ty0 = (int64_t)ty * TH, tx0 = (int64_t)tx * TW;
       const int64_t gy0 = ty0 - K + warp * PH, gx = tx0 - K + lane * CW;
-      if (pass > 0) {
+      if (pass > 0 && !tagged) {
         if (warp == 0 && !wait_neighbours(L.epoch, ty, tx, L.tiles_y, L.tiles_x, pass, lane, L.wait_ns) && lane == 0)
           record_status(L.status, GEO_ERR_TIMEOUT);
         __syncthreads();
       }
-      R::load_words(srcP, L.H, L.W, gy0, gx, pass > 0, false, w);
+      if (tagged && pass > 0) {
+        if (!R::load_tagged(R::tplane(L, (pass - 1) & 1), L.tpitch, L.H, L.W, gy0, gx, (unsigned)pass, L.wait_ns, w))
+          record_status(L.status, GEO_ERR_TIMEOUT);
+      } else {
+        R::load_words(srcP, L.H, L.W, gy0, gx, pass > 0, false, w);
+      }
       if (pass == 0 || !resident) R::load_words(L.mask, L.H, L.W, gy0, gx, false, true, m);
       if (pass == 0) q.init();
       else if (!resident) keys_load(q, L, Rp, Dp, ty0, tx0, lane, warp);
@@ -233,7 +243,10 @@ __global__ void __launch_bounds__(QP::NW * 32, 1) qdt_kernel(const TileLaunch L,
       }
       if (!ok) record_status(L.status, GEO_ERR_TIMEOUT);
       if (last || !resident) keys_store(q, L, Rp, Dp, ty0, tx0, lane, warp);
-      if (!last) {
+      if (!last && tagged) {
+        R::store_tagged(w, R::tplane(L, pass & 1), L.tpitch, L.H, L.W, ty0, tx0, K, TH, TW, (unsigned)(pass + 1), lane,
+                        warp);
+      } else if (!last) {
         R::store(w, dstP, dstP, false, L.H, L.W, ty0, tx0, K, TH, TW, lane, warp);
         __syncthreads();
         if (threadIdx.x == 0) st_release_u32(reinterpret_cast<unsigned *>(L.epoch) + t, (unsigned)(pass + 1));
@@ -322,15 +335,23 @@ int geo_qdt(geo_dtype dtype, const void *f, void *r, int32_t *d, int32_t *d_l1, 
   rc = plan_rr(GEO_U8, ERODE, 5, conn, H, W, S, &P);
   if (rc != GEO_OK) return rc;
 
-  // scratch: [control 256 B][per-tile epochs][two image buffers]
+  // scratch: [control 256 B][per-tile epochs][two tagged planes][two image buffers]
   const int64_t spitch = ((W + 15) / 16) * 16;
   const size_t ntiles = (size_t)P.tiles_x * (size_t)P.tiles_y;
   const size_t ctl_b = 256 + ((ntiles * sizeof(int) + 255) / 256) * 256;
   const size_t img_b = ((size_t)spitch * (size_t)H + 255) / 256 * 256;
+  const int64_t npasses = rr_passes(S, single_tile(P, 1) ? 0 : P.K);
+  // one tile per CTA and several passes: the passes hand over in two zeroed
+  // planes of tagged words (GEOMORPH_TAGGED=0: plain buffers and epochs)
+  const char *tg = getenv("GEOMORPH_TAGGED");
+  const bool tagged = ntiles <= (size_t)P.grid && npasses >= kTaggedMinPasses && P.K % 4 == 0 && P.TW % 4 == 0 &&
+                      !(tg && strcmp(tg, "0") == 0);
+  const int64_t tpitch = (W + 3) / 4;
+  const size_t tag_b = tagged ? ((2 * (size_t)tpitch * (size_t)H * 8 + 255) / 256) * 256 : 0;
   void *scratch = nullptr;
-  rc = pool_alloc(&scratch, ctl_b + 2 * img_b, s);
+  rc = pool_alloc(&scratch, ctl_b + tag_b + 2 * img_b, s);
   if (rc != GEO_OK) return rc;
-  if (cudaMemsetAsync(scratch, 0, ctl_b, s) != cudaSuccess) rc = GEO_ERR_CUDA;
+  if (cudaMemsetAsync(scratch, 0, ctl_b + tag_b, s) != cudaSuccess) rc = GEO_ERR_CUDA;
 
   auto plane = [](const void *p, int64_t pitch_b, size_t va) {
     Plane q;
@@ -344,8 +365,8 @@ int geo_qdt(geo_dtype dtype, const void *f, void *r, int32_t *d, int32_t *d_l1, 
   memset(&L, 0, sizeof(L));
   L.marker = plane(f, pitch, QP::CW);
   L.mask = plane(nullptr, 0, 1);
-  L.out = plane((char *)scratch + ctl_b, spitch, QP::CW);
-  L.scratch = plane((char *)scratch + ctl_b + img_b, spitch, QP::CW);
+  L.out = plane((char *)scratch + ctl_b + tag_b, spitch, QP::CW);
+  L.scratch = plane((char *)scratch + ctl_b + tag_b + img_b, spitch, QP::CW);
   L.H = H;
   L.W = W;
   L.TH = P.TH;
@@ -355,7 +376,12 @@ int geo_qdt(geo_dtype dtype, const void *f, void *r, int32_t *d, int32_t *d_l1, 
   L.tiles_y = P.tiles_y;
   L.mode = MODE_CHAIN;
   L.steps = S;
-  L.npasses = (int)rr_passes(S, single_tile(P, 1) ? 0 : P.K);
+  L.npasses = (int)npasses;
+  if (tagged) {
+    L.tagged = (unsigned long long *)((char *)scratch + ctl_b);
+    L.tpitch = tpitch;
+    L.tplane = tpitch * H;
+  }
   L.ctl = (Control *)scratch;
   L.epoch = (int *)((char *)scratch + 256);
   L.status = status;
