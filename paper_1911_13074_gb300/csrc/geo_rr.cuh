@@ -5,11 +5,12 @@
 // in the shared-memory tile kernel (geo_tile.cuh); what differs is where the
 // tile lives during the K steps: in registers. Chain passes synchronise
 // point to point (a tile waits for the 8 tiles its halo reads to publish the
-// previous pass: uint8 chains through tagged words that carry the pass that
-// wrote them, the others through per-tile epochs); reconstruction passes
-// meet at a grid barrier, test a
-// per-pass "changed" flag, and skip tiles whose 3x3 tile neighbourhood did
-// not change in the previous pass.
+// previous pass: uint8 and rank-code chains through tagged words that carry
+// the pass that wrote them, the others through per-tile epochs).
+// Reconstruction of one tile per CTA (uint8, rank codes) hands over the same
+// way and decides stability by a per-pass vote; otherwise its passes meet at
+// a grid barrier, test a per-pass "changed" flag, and skip tiles whose 3x3
+// tile neighbourhood did not change in the previous pass.
 //
 //   * A CTA holds a region of (32 * CW) x (NW * PH) pixels: warp w owns a
 //     horizontal band of PH pixel rows, lane l owns CW adjacent columns of it.
@@ -966,7 +967,7 @@ __device__ __forceinline__ int any_neighbour_changed(const int *flags, int ty, i
 }
 
 // ---------------------------------------------------------------------------
-// reconstruction with tagged planes (uint8, one tile per CTA)
+// reconstruction with tagged planes (uint8 or rank codes, one tile per CTA)
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned *p, unsigned v) {
